@@ -1,0 +1,34 @@
+"""Writes tests/golden/primes.json: seed-generated NTT-friendly primes per width.
+
+Calls only the oracle (gen_prime, two_adicity).  Run from the repository root:
+    python tests/golden/make_primes.py
+"""
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))))
+from oracle import gen_prime, two_adicity  # noqa: E402
+
+WIDTHS = (128, 256, 384, 768)
+SEEDS = (0, 1, 2, 3)
+
+
+def main():
+    out = {"comment": "q = c*2^32 + 1 with exactly W-4 bits (paper Sec. 5.2); c from "
+                      "random.Random('moma:<W>:<seed>'); Miller-Rabin accepted; written by "
+                      "tests/golden/make_primes.py from oracle.gen_prime",
+           "primes": []}
+    for w in WIDTHS:
+        for s in SEEDS:
+            q = gen_prime(w, s)
+            out["primes"].append({"width": w, "seed": s, "q": hex(q), "bits": q.bit_length(),
+                                  "two_adicity": two_adicity(q)})
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "primes.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+
+
+if __name__ == "__main__":
+    main()
