@@ -1,0 +1,392 @@
+"""Benchmark: 256-bit 2^20-point NTT throughput and 2^24-element mulmod throughput on GB300.
+
+One JSON line on rank 0.  `value` is forward 2^20-point NTTs per second over a 252-bit
+prime (256-bit container, L = 8 limbs), steady state over batches of 16 transforms per
+step (the paper reports steady-state batched runs, Sec. 5.1).  The mulmod figure
+(Gelem/s over 2^24 elements, same modulus) and its roofline are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: CUDA events on the launching stream, W untimed warm-up steps, K timed steps
+bracketed by a barrier and a device synchronisation; inputs are larger than L2 (512 MiB
+per NTT step, 1.5 GiB per mulmod step).  For N > 1 (torchrun) every rank runs its own
+replica (the work is independent per transform) and the time is the max over ranks.
+`--impl reference` times the CPU oracle (Python big integers) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "256-bit 2^20 NTT/s & mulmod Gelem/s vs roofline; batched/plain speedup; p99 latency"
+WIDTH = 256
+LOGN = 20
+NTT_BATCH = 16
+VEC_N = 1 << 24
+L = WIDTH // 32
+
+
+def word_products_per_mulmod(L):
+    """Algorithmic 32x32->64 word products of one L-limb modular multiplication: 2L^2 + L."""
+    return 2 * L * L + L
+
+
+def imad_per_mulmod(L):
+    return 2 * word_products_per_mulmod(L)  # a word product is a lo and a hi multiply-add
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def _oracle_ntt_worker(args):
+    q, logn, seed = args
+    import oracle
+    from paper_2501_07535_gb300 import inputs
+    x = inputs.to_ints(inputs.residues(q, L, 1 << logn, seed))
+    t = time.perf_counter()
+    oracle.ntt_fwd(x, q)
+    return time.perf_counter() - t
+
+
+def _oracle_mulmod_worker(args):
+    q, n, seed = args
+    import oracle
+    from paper_2501_07535_gb300 import inputs
+    a = inputs.to_ints(inputs.residues(q, L, n, seed))
+    b = inputs.to_ints(inputs.residues(q, L, n, seed + 1))
+    t = time.perf_counter()
+    oracle.vec_mulmod(a, b, q)
+    return time.perf_counter() - t
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_ntt_rate(pool, cores, q, logn=LOGN):
+    """All cores each run one full-size forward NTT; NTT/s = cores / wall time."""
+    t = time.perf_counter()
+    pool.map(_oracle_ntt_worker, [(q, logn, 1000 + i) for i in range(cores)])
+    wall = time.perf_counter() - t
+    return cores / wall, wall
+
+
+def oracle_mulmod_rate(pool, cores, q, n=1 << 19):
+    t = time.perf_counter()
+    pool.map(_oracle_mulmod_worker, [(q, n, 2000 + 2 * i) for i in range(cores)])
+    wall = time.perf_counter() - t
+    return cores * n / wall / 1e9, wall
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_07535_gb300 import build, inputs, moma
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+
+    # CPU oracle pool: spawned before any GPU work (rank 0 only)
+    pool = None
+    cores = _cores()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cores)
+
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    p = inputs.prime(WIDTH)
+    q = p.q
+    ctx = moma.moma_ctx_create(q, WIDTH)
+    st = torch.cuda.current_stream()
+    n = 1 << LOGN
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- inputs (resident in HBM)
+    xs = np.stack([inputs.residues(q, L, n, seed=10 + t + 100 * rank) for t in range(NTT_BATCH)])
+    dx = moma.to_device(xs, dev)
+    dy = torch.empty_like(dx)
+    a = moma.to_device(inputs.residues(q, L, VEC_N, seed=1 + 10 * rank), dev)
+    b = moma.to_device(inputs.residues(q, L, VEC_N, seed=2 + 10 * rank), dev)
+    c = torch.empty_like(a)
+
+    # plan set-up (twiddle tables) happens on the first call, outside the timed region
+    moma.moma_ntt_fwd_many(ctx, n, NTT_BATCH, dx, dy)
+    torch.cuda.synchronize()
+    n_pass_launches = _pass_count(LOGN, L)
+
+    # ---- IMAD peak probe (same run, same GPU)
+    probe_iters = 4000
+    pms, pimad = moma.moma_probe_imad(0, sms * 8, 256, probe_iters)
+    imad_peak = pimad / (pms * 1e-3)  # issues/s, chip-wide
+
+    # ---- NTT region
+    def ntt_step():
+        moma.moma_ntt_fwd_many(ctx, n, NTT_BATCH, dx, dy)
+
+    for _ in range(args.warmup):
+        ntt_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            ntt_step()
+        e1.record(st)
+        barrier()
+    ntt_ms = max_over_ranks(e0.elapsed_time(e1))
+    clocks = clk.summary()
+    ntt_per_s = world * NTT_BATCH * args.steps / (ntt_ms * 1e-3)
+
+    # ---- mulmod region
+    def mul_step():
+        moma.moma_vec_mulmod(ctx, VEC_N, a, b, c)
+
+    for _ in range(args.warmup):
+        mul_step()
+    barrier()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(st)
+    for _ in range(args.steps):
+        mul_step()
+    m1.record(st)
+    barrier()
+    mul_ms = max_over_ranks(m0.elapsed_time(m1))
+    gelem = world * VEC_N * args.steps / (mul_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
+    hx = torch.from_numpy(xs.view(np.int32)).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        dx.copy_(hx, non_blocking=True)
+        ntt_step()
+        hy.copy_(dy, non_blocking=True)
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for _ in range(args.steps):
+        dx.copy_(hx, non_blocking=True)
+        ntt_step()
+        hy.copy_(dy, non_blocking=True)
+    t1.record(st)
+    barrier()
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1))
+    e2e = world * NTT_BATCH * args.steps / (e2e_ms * 1e-3)
+    step_bytes = NTT_BATCH * L * n * 4
+
+    # ---- roofline
+    hbm = _measured_peaks().get("hbm_gbs")
+    mulmods_per_ntt = (n // 2) * LOGN
+    ntt_imad = imad_per_mulmod(L) * mulmods_per_ntt * NTT_BATCH
+    ntt_s_per_step = ntt_ms * 1e-3 / args.steps
+    ntt_achieved = ntt_imad / ntt_s_per_step / 1e12
+    peak_t = imad_peak / 1e12
+    mul_bytes = 3 * 4 * L * VEC_N
+    mul_imad = imad_per_mulmod(L) * VEC_N
+    mul_s = mul_ms * 1e-3 / args.steps
+    mul_roof_s = max(mul_bytes / (hbm * 1e9) if hbm else 0.0, mul_imad / imad_peak)
+    launches = args.steps * (n_pass_launches + 1)
+
+    result = {
+        "metric": METRIC,
+        "value": round(ntt_per_s, 2),
+        "unit": "NTT/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ntt_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic: seeded uniform residues mod a seed-generated 252-bit prime q = c*2^32+1",
+        "config": {"workload": f"forward cyclic NTT, n=2^{LOGN}, 256-bit container (252-bit prime), "
+                               f"{NTT_BATCH} transforms per step; mulmod on 2^24 elements, same prime",
+                   "n": n, "bits": WIDTH, "limbs": L, "batch": NTT_BATCH, "vec_n": VEC_N,
+                   "l2": "inputs larger than L2 (512 MiB per NTT step, 1.5 GiB per mulmod step)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": round(ntt_achieved, 3), "peak": round(peak_t, 3),
+                     "unit": "T IMAD/s", "frac": round(ntt_achieved / peak_t, 4), "traffic": None,
+                     "peak_source": "measured: moma_probe_imad carry-chain microbenchmark, same run",
+                     "algorithmic": f"(n/2)log2(n) mulmods x 2*(2L^2+L) IMAD = {imad_per_mulmod(L)} per mulmod"},
+        "mulmod": {"value": round(gelem, 3), "unit": "Gelem/s", "ms_per_step": round(mul_ms / args.steps, 4),
+                   "roofline": {"bound": "hbm" if mul_bytes / (hbm * 1e9 if hbm else 1) >= mul_imad / imad_peak
+                                else "alu",
+                                "time_us": round(mul_roof_s * 1e6, 2), "achieved_us": round(mul_s * 1e6, 2),
+                                "frac": round(mul_roof_s / mul_s, 4),
+                                "hbm_gbs_achieved": round(mul_bytes / mul_s / 1e9, 1), "hbm_gbs_peak": hbm,
+                                "imad_t_achieved": round(mul_imad / mul_s / 1e12, 3), "imad_t_peak": round(peak_t, 3)}},
+        "e2e": {"value": round(e2e, 2), "unit": "NTT/s", "h2d_bytes_per_step": step_bytes,
+                "d2h_bytes_per_step": step_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "imad_probe": {"ms": round(pms, 3), "imad": pimad, "t_imad_per_s": round(peak_t, 3), "sms": sms,
+                       "per_sm_per_clk": (round(imad_peak / sms / (clocks["sm_mhz"] * 1e6), 2)
+                                          if clocks.get("sm_mhz") else None)},
+    }
+    if pool is not None:
+        rate, wall = oracle_ntt_rate(pool, cores, q)
+        mrate, mwall = oracle_mulmod_rate(pool, cores, q)
+        pool.close()
+        result["cpu_baseline"] = {"value": round(rate, 4), "unit": "NTT/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"{cores} full 2^{LOGN}-point forward NTTs, one per core "
+                                            f"({wall:.1f} s wall)",
+                                  "mulmod": {"value": round(mrate, 6), "unit": "Gelem/s",
+                                             "sample": f"{cores} x 2^19-element mulmod ({mwall:.1f} s wall)"}}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    moma.moma_ctx_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _pass_count(logn, L):
+    tile = {4: 12, 8: 11, 12: 11}[L]
+    if logn <= tile:
+        return 1
+    return math.ceil(logn / (tile - 5))
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    from paper_2501_07535_gb300 import inputs
+    q = inputs.prime(WIDTH).q
+    cores = _cores()
+    pool = mp.get_context("spawn").Pool(cores)
+    for _ in range(args.warmup):
+        pool.map(_oracle_ntt_worker, [(q, LOGN - 4, 1 + i) for i in range(cores)])
+    t = time.perf_counter()
+    for k in range(args.steps):
+        pool.map(_oracle_ntt_worker, [(q, LOGN, 1000 + 100 * k + i) for i in range(cores)])
+    wall = time.perf_counter() - t
+    pool.close()
+    rate = cores * args.steps / wall
+    out = {"metric": METRIC, "value": round(rate, 4), "unit": "NTT/s", "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall / args.steps * 1e3, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "python-int",
+           "data": "synthetic: seeded uniform residues mod a seed-generated 252-bit prime",
+           "config": {"workload": f"forward cyclic NTT, n=2^{LOGN}, 256-bit container (252-bit prime), "
+                                  f"one transform per host core per step", "n": 1 << LOGN, "bits": WIDTH},
+           "cpu_baseline": {"value": round(rate, 4), "unit": "NTT/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} full 2^{LOGN}-point NTTs per step (warm-up steps at 2^{LOGN - 4})"},
+           "e2e": {"value": round(rate, 4), "unit": "NTT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * moma.h -- C ABI of the GB300 (sm_103a) multi-word modular arithmetic library.
+ *
+ * The operations are those of "Code Generation for Cryptographic Kernels using
+ * Multi-word Modular Arithmetic on GPU" (Zhang & Franchetti, CGO'25):
+ *   - element-wise modular BLAS over Z_q: addmod, submod, mulmod (Sec. 2.1, Eq. 1)
+ *     and axpy y' = a*x + y (Sec. 2.3);
+ *   - the forward cyclic number theoretic transform y(k) = sum_j x(j) w_n^(jk) mod q
+ *     (Sec. 2.3, Eq. ntt) and its inverse;
+ *   - the cyclic polynomial product through the transform (Sec. 2.3).
+ * Large-modulus arithmetic is broken into 32-bit machine words (Sec. 3, Eq. def_moma).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Widths.  bits in {128, 256, 384, 768}; L = bits/32 limbs of 32 bits.  The modulus
+ *   q must be odd and have exactly bits-4 bits (Sec. 5.2: a (k-4)-bit modulus for a
+ *   k-bit container, which the Barrett constants of Sec. 3.1 need); otherwise
+ *   MOMA_ERR_MODULUS.
+ * Layout.  A vector of n residues is limb-major: uint32 v[L][n], limb 0 the least
+ *   significant word of each residue (the paper writes words most significant first;
+ *   that is notation only).  Plane j of element i is at v[j*n + i].
+ * Values.  Inputs must be canonical, 0 <= x < q.  Outputs are canonical.  A
+ *   non-canonical input gives an unspecified (but memory-safe) result.
+ * Memory.  Vector arguments are device pointers owned by the caller; the library never
+ *   frees them.  They must be 4-byte aligned; 16-byte aligned planes (n a multiple of
+ *   4 and 16-byte aligned base) take the vectorised path.  Outputs may alias inputs
+ *   exactly (out == in); partial overlap is undefined.
+ * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *   asynchronous: the return code reports argument, configuration and launch errors
+ *   only.  Errors raised on the device (a bounded wait that ran out) are recorded in
+ *   the context and returned by moma_ctx_sync_status().
+ * Threads.  A context may be used from several host threads; plan creation is
+ *   serialised inside the context.  Calls that overlap on the device and write the same
+ *   buffers race, as with any CUDA kernel.
+ */
+#ifndef MOMA_H
+#define MOMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct moma_ctx moma_ctx;
+
+typedef enum {
+  MOMA_OK = 0,
+  MOMA_ERR_INVALID_ARG = 1, /* null pointer, bad width, n out of range for the call */
+  MOMA_ERR_MODULUS = 2,     /* q even, wrong bit length, or (for the NTT) not prime  */
+  MOMA_ERR_SIZE = 3,        /* NTT size not a power of two, > 2^24, or not | q-1     */
+  MOMA_ERR_ALIGN = 4,       /* device pointer not 4-byte aligned                     */
+  MOMA_ERR_OOM = 5,         /* device or host allocation failed                      */
+  MOMA_ERR_CUDA = 6,        /* a CUDA runtime call failed (launch, copy, event)      */
+  MOMA_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out                    */
+  MOMA_ERR_BUDGET = 8,      /* a job does not fit the memory budget it was given     */
+  MOMA_ERR_UNSUPPORTED = 9  /* valid request this build does not implement           */
+} moma_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *moma_status_string(moma_status s);
+
+/* ------------------------------------------------------------------ contexts */
+
+/* Create a context for modulus q (host array of bits/32 limbs, least significant
+ * first).  Precomputes the Barrett constant mu = floor(2^(2B+3)/q), B = bits-4
+ * (Sec. 3.1, Eq. mu) and the other per-modulus constants, and uploads them.  Transform
+ * plans (twiddle tables) are built lazily per size.  *out receives the context; it is
+ * set to NULL on error.  Uses the current CUDA device. */
+moma_status moma_ctx_create(const uint32_t *q, int bits, moma_ctx **out);
+
+/* Release the context, its plans and device tables.  Safe on NULL.  The caller must
+ * ensure no work using the context is still running. */
+void moma_ctx_destroy(moma_ctx *ctx);
+
+/* Number of 32-bit limbs L of the context (0 for NULL). */
+int moma_ctx_limbs(const moma_ctx *ctx);
+
+/* Write the primitive n-th root of unity w_n the transforms use (L host limbs):
+ * w_n = g^((q-1)/n) with g the smallest integer >= 2 that is a quadratic non-residue
+ * mod q (the paper leaves the choice of root open, Sec. 2.3).  n a power of two
+ * dividing q-1, 2 <= n <= 2^24. */
+moma_status moma_ctx_root(moma_ctx *ctx, size_t n, uint32_t *w_out);
+
+/* Block until all work the context issued is done and return (then clear) the first
+ * device-side error recorded since the last call (MOMA_ERR_TIMEOUT), else MOMA_OK. */
+moma_status moma_ctx_sync_status(moma_ctx *ctx);
+
+/* ------------------------------------------------------------------ modular BLAS */
+
+/* c[i] = a[i] + b[i] mod q, i < n (Sec. 2.1 Eq. 1 and Eq. saddmod).  n may be 0. */
+moma_status moma_vec_addmod(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
+                            uint32_t *c, void *stream);
+
+/* c[i] = a[i] - b[i] mod q (Sec. 2.1 Eq. 1 and Eq. ssubmod). */
+moma_status moma_vec_submod(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
+                            uint32_t *c, void *stream);
+
+/* c[i] = a[i] * b[i] mod q by multi-word Barrett reduction (Sec. 3.1 Eq. barrett and
+ * Eq. mu; Sec. 3.2 Listing dmulmod generalised to L words). */
+moma_status moma_vec_mulmod(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
+                            uint32_t *c, void *stream);
+
+/* out[i] = alpha * x[i] + y[i] mod q (Sec. 2.3, BLAS axpy).  alpha: HOST array of L
+ * limbs, canonical.  out may alias y (the BLAS in-place form) or x. */
+moma_status moma_vec_axpymod(moma_ctx *ctx, size_t n, const uint32_t *alpha, const uint32_t *x,
+                             const uint32_t *y, uint32_t *out, void *stream);
+
+/* ------------------------------------------------------------------ transforms */
+
+/* Forward cyclic NTT of length n (Sec. 2.3 Eq. ntt), natural order in and out:
+ * out[k] = sum_j in[j] w_n^(jk) mod q.  n a power of two, 2 <= n <= 2^24, n | q-1,
+ * q prime.  in/out: L*n words each; out may equal in. */
+moma_status moma_ntt_fwd(moma_ctx *ctx, size_t n, const uint32_t *in, uint32_t *out,
+                         void *stream);
+
+/* Inverse: out[j] = n^-1 sum_k in[k] w_n^(-jk) mod q. */
+moma_status moma_ntt_inv(moma_ctx *ctx, size_t n, const uint32_t *in, uint32_t *out,
+                         void *stream);
+
+/* `count` independent transforms of length n in one launch sequence: transform t reads
+ * in + t*L*n and writes out + t*L*n (each transform limb-major on its own). */
+moma_status moma_ntt_fwd_many(moma_ctx *ctx, size_t n, size_t count, const uint32_t *in,
+                              uint32_t *out, void *stream);
+moma_status moma_ntt_inv_many(moma_ctx *ctx, size_t n, size_t count, const uint32_t *in,
+                              uint32_t *out, void *stream);
+
+/* Cyclic product c = a * b mod (x^n - 1, q) = INTT(NTT(a) . NTT(b)) (Sec. 2.3,
+ * polynomial multiplication through the transform); the pointwise product is fused
+ * into the first pass of the inverse transform.  a, b, c: L*n words; c may alias a or b. */
+moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
+                         uint32_t *c, void *stream);
+
+/* ------------------------------------------------------------------ measurement */
+
+/* Integer multiply-add issue-rate microbenchmark (used for the compute roofline).
+ * Runs `blocks` x `threads` threads, each issuing `iters` rounds of a fixed block of
+ * mad.lo.cc / madc.hi.cc carry chains (variant 0: 8 independent chains per thread;
+ * variant 1: one dependent chain).  Writes the kernel time in milliseconds and the
+ * number of 32-bit multiply-add instructions it issued.  Synchronous. */
+moma_status moma_probe_imad(int variant, int blocks, int threads, int iters, double *ms_out,
+                            double *imad_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOMA_H */

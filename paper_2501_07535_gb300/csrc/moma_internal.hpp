@@ -1,0 +1,86 @@
+// moma_internal.hpp -- context, plans and launcher declarations shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "../../include/moma.h"
+#include "moma_bigint.hpp"
+
+namespace moma {
+
+constexpr int kMaxL = 24;
+constexpr int kMaxLogN = 24;
+
+// Host copy of the per-modulus constants (device code receives ModK<L> by value).
+struct HostConsts {
+  int L = 0;
+  uint32_t q[kMaxL] = {}, nq[kMaxL] = {}, mu[kMaxL] = {}, q2[kMaxL] = {};
+  uint32_t R0[kMaxL] = {};  // 2^(32L) mod q
+  uint32_t Q0 = 0;          // floor(2^(32L) / q)  (between 16 and 31)
+};
+
+// One Stockham pass: radix 2^logR over groups of stride n/R, after logNs radix bits.
+struct PassDesc {
+  int logR = 0, logNs = 0, logG = 0;
+  uint32_t* tw_pass = nullptr;  // [2L][tw_count], null when Ns == 1
+  uint32_t* tw_int = nullptr;   // [2L][R/2]
+  uint64_t tw_count = 0;
+};
+
+struct Plan {
+  int logn = 0;
+  bool inverse = false;
+  std::vector<PassDesc> passes;
+  uint32_t* d_tables = nullptr;  // one allocation holding every table of the plan
+  uint32_t scale[kMaxL] = {}, scalep[kMaxL] = {};  // n^-1 and its companion (inverse)
+  int tile_log = 0;                                // log2 of the CTA tile (elements)
+};
+
+}  // namespace moma
+
+struct moma_ctx {
+  int L = 0;
+  int bits = 0;
+  int device = 0;
+  int num_sms = 0;
+  moma::HostConsts k;
+  moma::BigU Q;
+  moma::Reducer* red = nullptr;  // host reductions mod q
+  // transform state, filled on first use
+  std::mutex lock;
+  int ntt_ready = 0;  // 0: not yet, 1: ok, -1: modulus not prime
+  uint32_t g = 0;     // smallest quadratic non-residue
+  int two_adicity = 0;
+  std::map<std::pair<int, int>, moma::Plan*> plans;  // (logn, inverse) -> plan
+  int* d_status = nullptr;                            // device-side error word
+};
+
+namespace moma {
+
+// Status helpers
+inline moma_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MOMA_OK : MOMA_ERR_CUDA; }
+
+// moma_blas.cu
+enum VecOp { VEC_ADD = 0, VEC_SUB = 1, VEC_MUL = 2, VEC_AXPY = 3 };
+moma_status launch_vec(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
+                       uint32_t* c, const uint32_t* alpha_host, cudaStream_t st);
+
+// moma_ntt.cu
+moma_status ntt_prepare(moma_ctx* ctx);  // primality, generator (takes ctx->lock)
+moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, Plan** out);
+moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in,
+                       uint32_t* out, cudaStream_t st);
+moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
+                           uint32_t* c, cudaStream_t st);
+void free_plan(Plan* p);
+BigU root_of_unity(moma_ctx* ctx, int logn);  // requires ntt_prepare()
+
+// Shoup-style companion floor(w * 2^(32L) / q) for a host constant w < q.
+void companion(const moma_ctx* ctx, const BigU& w, uint32_t* out);
+
+}  // namespace moma

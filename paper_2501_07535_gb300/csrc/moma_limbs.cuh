@@ -1,0 +1,332 @@
+// moma_limbs.cuh -- multi-word modular arithmetic on 32-bit machine words (device code).
+//
+// A residue of a W-bit container is L = W/32 words x[0..L), x[0] least significant
+// (Sec. 3, Eq. def_moma writes the same words most significant first).  The modulus q
+// has exactly B = W - 4 bits (Sec. 5.2), which leaves 4 bits of headroom in the top word:
+// a sum of two residues never carries out of the container, so the carry word of rule
+// (moddq_add) is always zero here and is not materialised.
+//
+// Word-level building blocks follow the rewrite rules of Table 1:
+//   (addqdd)+(adc)  multi-word addition        -> add_words  (one add.cc/addc.cc chain)
+//   (subddd)        multi-word subtraction     -> sub_words  (one sub.cc/subc.cc chain)
+//   (ltd)+(eqd)     multi-word comparison      -> the borrow out of sub_words
+//   (moddq_add)     reduction after an add     -> cond_sub
+//   (mulqdd)+(addqqq) schoolbook multiplication -> mul_full / mul_lo_acc / mul_hi_trunc
+// add_words/sub_words are written as the recursion the paper formalises (Sec. 3.2 "MoMA
+// via recursion"): split the operand into a low and a high part, process the low part,
+// feed its carry into the high part, and recurse until one machine word remains.  For a
+// width that is not a power of two (384, 768 bits) the split takes the largest power of
+// two below L for the low part, which is the zero-word pruning of Sec. 4
+// ("Non-power-of-two input bit-widths") done at compile time.
+//
+// Products use operand scanning: row i adds x_i * y into the accumulator with one
+// mad.lo.cc chain (low halves of the word products) and one mad.hi.cc chain (high
+// halves).  The leaves of rule (mulqdd)'s recursion are exactly these L^2 word products;
+// the GPU's multiply-add-with-carry performs the additions of rules (addqdd)/(addqqq) in
+// the same instruction, so no separate addition chains are emitted.
+//
+// Every statement that reads or writes the PTX carry flag is `asm volatile`, which keeps
+// the chains in program order in the front end; ptxas tracks the carry dependency.
+
+#pragma once
+#include <stdint.h>
+
+#ifndef MOMA_DEV
+#define MOMA_DEV __device__ __forceinline__
+#endif
+
+namespace moma {
+
+// ------------------------------------------------------------------ PTX carry primitives
+#ifndef MOMA_HOST_PRIMITIVES
+MOMA_DEV uint32_t add_cc(uint32_t a, uint32_t b) {
+  uint32_t r; asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
+}
+MOMA_DEV uint32_t addc_cc(uint32_t a, uint32_t b) {
+  uint32_t r; asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
+}
+MOMA_DEV uint32_t addc(uint32_t a, uint32_t b) {
+  uint32_t r; asm volatile("addc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
+}
+MOMA_DEV uint32_t sub_cc(uint32_t a, uint32_t b) {
+  uint32_t r; asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
+}
+MOMA_DEV uint32_t subc_cc(uint32_t a, uint32_t b) {
+  uint32_t r; asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
+}
+MOMA_DEV uint32_t subc(uint32_t a, uint32_t b) {
+  uint32_t r; asm volatile("subc.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b)); return r;
+}
+// r = lo(a*b) + c, carry out
+MOMA_DEV uint32_t mad_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r; asm volatile("mad.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r;
+}
+MOMA_DEV uint32_t madc_lo_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r; asm volatile("madc.lo.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r;
+}
+MOMA_DEV uint32_t madc_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r; asm volatile("madc.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r;
+}
+MOMA_DEV uint32_t mad_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r; asm volatile("mad.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r;
+}
+MOMA_DEV uint32_t madc_hi_cc(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r; asm volatile("madc.hi.cc.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r;
+}
+MOMA_DEV uint32_t madc_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r; asm volatile("madc.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c)); return r;
+}
+MOMA_DEV uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
+MOMA_DEV uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) { return __umulhi(a, b) + c; }
+// (hi:lo) >> s for 0 <= s < 32
+MOMA_DEV uint32_t shr_pair(uint32_t lo, uint32_t hi, uint32_t s) { return __funnelshift_r(lo, hi, s); }
+#endif
+
+// Carry (0/1) left in the flag by the last chain.
+MOMA_DEV uint32_t carry_out() { return addc(0u, 0u); }
+// Borrow mask left by the last subtraction chain: 0xffffffff if it borrowed, else 0.
+MOMA_DEV uint32_t borrow_mask() { return subc(0u, 0u); }
+
+// Compile-time loop: f(IntC<i>{}) for i = I..E-1, so that the index can be a template argument.
+template <int V>
+struct IntC {
+  static constexpr int value = V;
+};
+template <int I, int E, typename F>
+MOMA_DEV void static_for(F&& f) {
+  if constexpr (I < E) {
+    f(IntC<I>{});
+    static_for<I + 1, E>(static_cast<F&&>(f));
+  }
+}
+
+// Largest power of two strictly below n (n >= 2): the low part of one recursion step.
+template <int N>
+constexpr int low_split() {
+  int p = 1;
+  while (p * 2 < N) p *= 2;
+  return p;
+}
+
+// ------------------------------------------------------------------ rules (addqdd)/(adc)
+// c = a + b over N words; CIN: a carry is pending in the flag from a lower part.
+template <int N, bool CIN>
+MOMA_DEV void add_words(uint32_t* c, const uint32_t* a, const uint32_t* b) {
+  if constexpr (N == 1) {
+    c[0] = CIN ? addc_cc(a[0], b[0]) : add_cc(a[0], b[0]);
+  } else {
+    constexpr int H = low_split<N>();
+    add_words<H, CIN>(c, a, b);
+    add_words<N - H, true>(c + H, a + H, b + H);
+  }
+}
+
+// ------------------------------------------------------------------ rule (subddd)
+template <int N, bool BIN>
+MOMA_DEV void sub_words(uint32_t* c, const uint32_t* a, const uint32_t* b) {
+  if constexpr (N == 1) {
+    c[0] = BIN ? subc_cc(a[0], b[0]) : sub_cc(a[0], b[0]);
+  } else {
+    constexpr int H = low_split<N>();
+    sub_words<H, BIN>(c, a, b);
+    sub_words<N - H, true>(c + H, a + H, b + H);
+  }
+}
+
+// ------------------------------------------------------------------ rule (moddq_add)
+// x <- x - m when x >= m; valid for x < 2m.  The comparison of rules (ltd)/(eqd) is the
+// borrow of the trial subtraction; the select is per word.
+template <int L>
+MOMA_DEV void cond_sub(uint32_t (&x)[L], const uint32_t* m) {
+  uint32_t d[L];
+  sub_words<L, false>(d, x, m);
+  const uint32_t keep = borrow_mask();
+#pragma unroll
+  for (int i = 0; i < L; ++i) x[i] = (x[i] & keep) | (d[i] & ~keep);
+}
+
+// c = a + b mod q for canonical a, b (Eq. saddmod with the >= reading).
+template <int L>
+MOMA_DEV void addmod(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                     const uint32_t* q) {
+  add_words<L, false>(c, a, b);
+  cond_sub<L>(c, q);
+}
+
+// c = a - b mod q for canonical a, b (Eq. ssubmod): add q back when the subtraction borrowed.
+template <int L>
+MOMA_DEV void submod(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                     const uint32_t* q) {
+  sub_words<L, false>(c, a, b);
+  const uint32_t m = borrow_mask();
+  uint32_t t[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) t[i] = q[i] & m;
+  add_words<L, false>(c, c, t);
+}
+
+// ------------------------------------------------------------------ product rows
+// r[k] += lo(x * y[k]), k < N, as one chain.  KEEP: leave the top carry in the flag.
+template <int N, bool KEEP>
+MOMA_DEV void row_lo(uint32_t* r, uint32_t x, const uint32_t* y) {
+  if constexpr (N == 1 && !KEEP) {
+    r[0] = mad_lo(x, y[0], r[0]);
+  } else {
+    r[0] = mad_lo_cc(x, y[0], r[0]);
+#pragma unroll
+    for (int k = 1; k < N - 1; ++k) r[k] = madc_lo_cc(x, y[k], r[k]);
+    if constexpr (N > 1) r[N - 1] = KEEP ? madc_lo_cc(x, y[N - 1], r[N - 1]) : madc_lo(x, y[N - 1], r[N - 1]);
+  }
+}
+
+// r[k] += hi(x * y[k]), k < N, as one chain.
+template <int N, bool KEEP>
+MOMA_DEV void row_hi(uint32_t* r, uint32_t x, const uint32_t* y) {
+  if constexpr (N == 1 && !KEEP) {
+    r[0] = mad_hi(x, y[0], r[0]);
+  } else {
+    r[0] = mad_hi_cc(x, y[0], r[0]);
+#pragma unroll
+    for (int k = 1; k < N - 1; ++k) r[k] = madc_hi_cc(x, y[k], r[k]);
+    if constexpr (N > 1) r[N - 1] = KEEP ? madc_hi_cc(x, y[N - 1], r[N - 1]) : madc_hi(x, y[N - 1], r[N - 1]);
+  }
+}
+
+// ------------------------------------------------------------------ Eq. muls, full product
+// t[0..2L) = x * y (schoolbook, L^2 word products).
+// Invariant before row i: t[0..i+L) holds the partial sum, t[i+L] is free.
+template <int L>
+MOMA_DEV void mul_full(uint32_t (&t)[2 * L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+#pragma unroll
+  for (int k = 0; k < L; ++k) t[k] = x[0] * y[k];
+#pragma unroll
+  for (int k = L; k < 2 * L; ++k) t[k] = 0u;
+  row_hi<L, false>(t + 1, x[0], y);  // t[L] = hi(x0*y[L-1]) + carry: no carry out
+#pragma unroll
+  for (int i = 1; i < L; ++i) {
+    row_lo<L, true>(t + i, x[i], y);
+    t[i + L] = carry_out();
+    row_hi<L, false>(t + i + 1, x[i], y);  // ends in t[i+L]; the partial sum fits i+L+1 words
+  }
+}
+
+// r = r + x * y mod 2^(32L): only the word products below the container's top.
+template <int L>
+MOMA_DEV void mul_lo_acc(uint32_t (&r)[L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  static_for<0, L>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    row_lo<L - i, false>(r + i, x[i], y);
+    if constexpr (i < L - 1) row_hi<L - 1 - i, false>(r + i + 1, x[i], y);
+  });
+}
+
+// H ~= floor(x * y / 2^(32L)) from the columns >= L-1 of the product plus the high halves
+// of column L-2.  The dropped part is below 2L * 2^(32(L-1)) < 2^(32L), so H is the exact
+// floor or one less.  A[p] holds product word L-1+p, p = 0..L.
+template <int L>
+MOMA_DEV void mul_hi_trunc(uint32_t (&H)[L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  uint32_t A[L + 1];
+#pragma unroll
+  for (int p = 0; p <= L; ++p) A[p] = 0u;
+  // row 0: lo(x0*y[L-1]) at p=0; hi(x0*y[L-2]) at p=0, hi(x0*y[L-1]) at p=1
+  A[0] = x[0] * y[L - 1];
+  row_hi<2, false>(A, x[0], y + (L - 2));
+  static_for<1, L>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    if constexpr (i < L - 1) {
+      // lo terms j = L-1-i .. L-1 -> p = 0..i ; hi terms j = L-2-i .. L-1 -> p = 0..i+1
+      row_lo<i + 1, true>(A, x[i], y + (L - 1 - i));
+      A[i + 1] = carry_out();
+      row_hi<i + 2, false>(A, x[i], y + (L - 2 - i));
+    } else {
+      // last row: lo terms j = 0..L-1 -> p = 0..L-1 ; hi terms -> p = 1..L
+      row_lo<L, true>(A, x[i], y);
+      A[L] = carry_out();
+      row_hi<L, false>(A + 1, x[i], y);
+    }
+  });
+#pragma unroll
+  for (int k = 0; k < L; ++k) H[k] = A[k + 1];
+}
+
+// ------------------------------------------------------------------ per-modulus constants
+// Kernel-parameter copy of the constants of one modulus (lives in the constant bank).
+template <int L>
+struct ModK {
+  uint32_t q[L];    // modulus, B = 32L - 4 bits
+  uint32_t nq[L];   // 2^(32L) - q, so that  t - s*q = t + s*nq  mod 2^(32L)
+  uint32_t mu[L];   // Barrett constant floor(2^(2B+3) / q)  (Eq. mu, k = 2B+3)
+  uint32_t q2[L];   // 2q
+};
+
+// ------------------------------------------------------------------ Sec. 3.1, Eq. barrett
+// Barrett reduction of a double-width product t < q^2 with the shifts of Listing 1
+// generalised to L words (Listing dmulmod does the same at two words):
+//   t1 = t >> (B-2);  s = (t1 * mu) >> (B+5);  c = t - s*q;  if c >= q: c -= q.
+// B-2 = 32(L-1) + 26 and B+5 = 32L + 1, so t1 is words L-1..2L-1 shifted by 26 bits and
+// s is the high half of t1*mu shifted by one bit.  Only the low L words of t - s*q are
+// formed ("the first half matches", Listing dmulmod), as c < 2q < 2^(32L).
+// The high half of t1*mu comes from mul_hi_trunc; its error (< L*2^-32 of one unit after
+// the shift) keeps c below 2q, so one correction suffices as in Listing 1.
+// Returns the quotient estimate s in `s` (callers that need floor(t/q) add the correction).
+template <int L>
+MOMA_DEV uint32_t barrett_reduce(uint32_t (&c)[L], uint32_t (&s)[L], const uint32_t (&t)[2 * L],
+                                 const ModK<L>& k) {
+  uint32_t t1[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) t1[i] = shr_pair(t[L - 1 + i], t[L + i], 26u);
+  uint32_t h[L];
+  mul_hi_trunc<L>(h, t1, k.mu);
+#pragma unroll
+  for (int i = 0; i < L - 1; ++i) s[i] = shr_pair(h[i], h[i + 1], 1u);
+  s[L - 1] = h[L - 1] >> 1;
+#pragma unroll
+  for (int i = 0; i < L; ++i) c[i] = t[i];
+  mul_lo_acc<L>(c, s, k.nq);
+  // final correction (the conditional subtraction of Listing 1); report whether it fired
+  uint32_t d[L];
+  sub_words<L, false>(d, c, k.q);
+  const uint32_t keep = borrow_mask();
+#pragma unroll
+  for (int i = 0; i < L; ++i) c[i] = (c[i] & keep) | (d[i] & ~keep);
+  return ~keep & 1u;
+}
+
+// c = a * b mod q (Eq. barrett).
+template <int L>
+MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                             const ModK<L>& k) {
+  uint32_t t[2 * L];
+  mul_full<L>(t, a, b);
+  uint32_t s[L];
+  barrett_reduce<L>(c, s, t, k);
+}
+
+// ------------------------------------------------------------------ fixed multiplicand
+// Barrett with the quotient of the constant precomputed: for a fixed canonical w and its
+// companion wp = floor(w * 2^(32L) / q), the quotient of a*w by q is estimated by the high
+// half of a*wp, so the reduction needs no double-width product of a*w:
+//   s = floor(a*wp / 2^(32L)) (truncated, exact or one less);  r = a*w - s*q mod 2^(32L).
+// For any a < 2^(32L): a*w/q - s < 3, so r lies in [0, 3q), which fits the container.
+// Used for twiddle factors (tables carry the companion) and for the axpy scalar.
+template <int L>
+MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
+                                const uint32_t (&wp)[L], const ModK<L>& k) {
+  uint32_t s[L];
+  mul_hi_trunc<L>(s, a, wp);
+#pragma unroll
+  for (int i = 0; i < L; ++i) r[i] = 0u;
+  mul_lo_acc<L>(r, a, w);
+  mul_lo_acc<L>(r, s, k.nq);
+}
+
+// Canonical form: r in [0, 3q) -> [0, q).
+template <int L>
+MOMA_DEV void mulmod_fixed(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
+                           const uint32_t (&wp)[L], const ModK<L>& k) {
+  mulmod_fixed_lazy<L>(r, a, w, wp, k);
+  cond_sub<L>(r, k.q2);  // [0,3q) -> [0,2q)
+  cond_sub<L>(r, k.q);   // -> [0,q)
+}
+
+}  // namespace moma

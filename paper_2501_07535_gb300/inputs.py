@@ -114,36 +114,42 @@ def prime(width: int, seed: int = 0) -> Prime:
 
 # ----------------------------------------------------------------------------- residues
 
+def _less_than(draw: np.ndarray, ql: list[int]) -> np.ndarray:
+    """Column-wise draw < q, comparing limbs from the most significant one down."""
+    L = draw.shape[0]
+    less = draw[L - 1] < np.uint32(ql[L - 1])
+    tie = np.nonzero(draw[L - 1] == np.uint32(ql[L - 1]))[0]
+    for j in range(L - 2, -1, -1):
+        if tie.size == 0:
+            break
+        col = draw[j, tie]
+        less[tie[col < np.uint32(ql[j])]] = True
+        tie = tie[col == np.uint32(ql[j])]
+    return less
+
+
 def residues(q: int, L: int, n: int, seed: int) -> np.ndarray:
     """n residues uniform in [0, q) as uint32[L][n], from numpy PCG64(seed).
 
     Raw limbs are drawn uniformly, the top limb masked to the bit length of q, and
     columns that are >= q are redrawn (rejection keeps the distribution exactly
-    uniform).  The comparison with q is a lexicographic scan from the top limb.
+    uniform).  The comparison with q is lexicographic from the top limb.
     """
     if q <= 0 or q.bit_length() > 32 * L:
         raise ValueError("q does not fit in L limbs")
+    top_bits = q.bit_length() - 32 * (L - 1)
+    if top_bits <= 0:
+        raise ValueError("q shorter than L-1 limbs; use fewer limbs")
+    mask = np.uint32((1 << top_bits) - 1) if top_bits < 32 else np.uint32(0xFFFFFFFF)
     rng = np.random.Generator(np.random.PCG64(seed))
-    qb = q.bit_length()
-    top_bits = qb - 32 * (L - 1)
     ql = int_to_limbs(q, L)
-    out = np.zeros((L, n), dtype=np.uint32)
-    todo = np.arange(n, dtype=np.int64)
+    out = rng.integers(0, 1 << 32, size=(L, n), dtype=np.uint32)
+    out[L - 1] &= mask
+    todo = np.nonzero(~_less_than(out, ql))[0]
     while todo.size:
-        draw = rng.integers(0, 1 << 32, size=(L, todo.size), dtype=np.uint64).astype(np.uint32)
-        if top_bits <= 0:
-            raise ValueError("q shorter than L-1 limbs; use fewer limbs")
-        if top_bits < 32:
-            draw[L - 1] &= np.uint32((1 << top_bits) - 1)
-        # lexicographic compare draw < q from the most significant limb down
-        less = np.zeros(todo.size, dtype=bool)
-        undecided = np.ones(todo.size, dtype=bool)
-        for j in range(L - 1, -1, -1):
-            lt = draw[j] < np.uint32(ql[j])
-            gt = draw[j] > np.uint32(ql[j])
-            less |= undecided & lt
-            undecided &= ~(lt | gt)
-        ok = less
+        draw = rng.integers(0, 1 << 32, size=(L, todo.size), dtype=np.uint32)
+        draw[L - 1] &= mask
+        ok = _less_than(draw, ql)
         out[:, todo[ok]] = draw[:, ok]
         todo = todo[~ok]
     return out

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libmoma.so (include/moma.h), same names as the C ABI.
+
+Argument marshalling only: every step of the arithmetic runs in the library's CUDA
+kernels.  PyTorch supplies device memory (tensors are passed by data pointer) and
+streams.  If the shared library is missing the import of this module still works, but
+the first call raises: there is no CPU fallback.
+
+Vectors are torch tensors on the GPU with dtype int32 or uint32 holding the raw 32-bit
+limbs, shape (L, n) limb-major (limb 0 least significant), or (count, L, n) for the
+batched transforms.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmoma.so")
+
+STATUS = {0: "MOMA_OK", 1: "MOMA_ERR_INVALID_ARG", 2: "MOMA_ERR_MODULUS", 3: "MOMA_ERR_SIZE",
+          4: "MOMA_ERR_ALIGN", 5: "MOMA_ERR_OOM", 6: "MOMA_ERR_CUDA", 7: "MOMA_ERR_TIMEOUT",
+          8: "MOMA_ERR_BUDGET", 9: "MOMA_ERR_UNSUPPORTED"}
+MOMA_OK = 0
+
+
+class MomaError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_SIGS = {
+    "moma_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "moma_ctx_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "moma_ctx_destroy": (None, [_P]),
+    "moma_ctx_limbs": (ctypes.c_int, [_P]),
+    "moma_ctx_root": (ctypes.c_int, [_P, _SZ, _P]),
+    "moma_ctx_sync_status": (ctypes.c_int, [_P]),
+    "moma_vec_addmod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
+    "moma_vec_submod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
+    "moma_vec_mulmod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
+    "moma_vec_axpymod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P, _P]),
+    "moma_ntt_fwd": (ctypes.c_int, [_P, _SZ, _P, _P, _P]),
+    "moma_ntt_inv": (ctypes.c_int, [_P, _SZ, _P, _P, _P]),
+    "moma_ntt_fwd_many": (ctypes.c_int, [_P, _SZ, _SZ, _P, _P, _P]),
+    "moma_ntt_inv_many": (ctypes.c_int, [_P, _SZ, _SZ, _P, _P, _P]),
+    "moma_polymul": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
+    "moma_probe_imad": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmoma.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2501_07535_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(code: int, what: str):
+    if code != MOMA_OK:
+        raise MomaError(code, what)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise TypeError("expected int32/uint32 limbs")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _limbs_array(x: int, L: int):
+    arr = (ctypes.c_uint32 * L)(*inputs.int_to_limbs(x, L))
+    return arr
+
+
+# ----------------------------------------------------------------- C-ABI names
+
+def moma_status_string(code: int) -> str:
+    return lib().moma_status_string(code).decode()
+
+
+def moma_ctx_create(q: int, bits: int) -> int:
+    L = bits // 32
+    h = _P()
+    qa = _limbs_array(q, L)
+    _check(lib().moma_ctx_create(ctypes.cast(qa, _P), bits, ctypes.byref(h)), "moma_ctx_create")
+    return h.value
+
+
+def moma_ctx_destroy(ctx: int):
+    lib().moma_ctx_destroy(ctx)
+
+
+def moma_ctx_limbs(ctx: int) -> int:
+    return lib().moma_ctx_limbs(ctx)
+
+
+def moma_ctx_root(ctx: int, n: int) -> int:
+    L = moma_ctx_limbs(ctx)
+    out = (ctypes.c_uint32 * L)()
+    _check(lib().moma_ctx_root(ctx, n, ctypes.cast(out, _P)), "moma_ctx_root")
+    return inputs.limbs_to_int(list(out))
+
+
+def moma_ctx_sync_status(ctx: int) -> int:
+    return lib().moma_ctx_sync_status(ctx)
+
+
+def moma_vec_addmod(ctx, n, a, b, c, stream=None):
+    _check(lib().moma_vec_addmod(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), "moma_vec_addmod")
+
+
+def moma_vec_submod(ctx, n, a, b, c, stream=None):
+    _check(lib().moma_vec_submod(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), "moma_vec_submod")
+
+
+def moma_vec_mulmod(ctx, n, a, b, c, stream=None):
+    _check(lib().moma_vec_mulmod(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), "moma_vec_mulmod")
+
+
+def moma_vec_axpymod(ctx, n, alpha: int, x, y, out, stream=None):
+    al = _limbs_array(alpha, moma_ctx_limbs(ctx))
+    _check(lib().moma_vec_axpymod(ctx, n, ctypes.cast(al, _P), _ptr(x), _ptr(y), _ptr(out),
+                                  _stream_handle(stream)), "moma_vec_axpymod")
+
+
+def moma_ntt_fwd(ctx, n, x, y, stream=None):
+    _check(lib().moma_ntt_fwd(ctx, n, _ptr(x), _ptr(y), _stream_handle(stream)), "moma_ntt_fwd")
+
+
+def moma_ntt_inv(ctx, n, x, y, stream=None):
+    _check(lib().moma_ntt_inv(ctx, n, _ptr(x), _ptr(y), _stream_handle(stream)), "moma_ntt_inv")
+
+
+def moma_ntt_fwd_many(ctx, n, count, x, y, stream=None):
+    _check(lib().moma_ntt_fwd_many(ctx, n, count, _ptr(x), _ptr(y), _stream_handle(stream)), "moma_ntt_fwd_many")
+
+
+def moma_ntt_inv_many(ctx, n, count, x, y, stream=None):
+    _check(lib().moma_ntt_inv_many(ctx, n, count, _ptr(x), _ptr(y), _stream_handle(stream)), "moma_ntt_inv_many")
+
+
+def moma_polymul(ctx, n, a, b, c, stream=None):
+    _check(lib().moma_polymul(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), "moma_polymul")
+
+
+def moma_probe_imad(variant: int, blocks: int, threads: int, iters: int):
+    ms = ctypes.c_double()
+    cnt = ctypes.c_double()
+    _check(lib().moma_probe_imad(variant, blocks, threads, iters, ctypes.byref(ms), ctypes.byref(cnt)),
+           "moma_probe_imad")
+    return ms.value, cnt.value
+
+
+# ----------------------------------------------------------------- conveniences
+
+def to_device(arr: np.ndarray, device="cuda"):
+    """uint32 numpy array -> int32 CUDA tensor with the same bits."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(arr, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def to_host(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+class Context:
+    """Owns one moma_ctx (one modulus)."""
+
+    def __init__(self, q: int, bits: int):
+        self.q = q
+        self.bits = bits
+        self.L = bits // 32
+        self.handle = moma_ctx_create(q, bits)
+
+    def close(self):
+        if self.handle:
+            moma_ctx_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def root(self, n: int) -> int:
+        return moma_ctx_root(self.handle, n)
+
+    def sync_status(self) -> int:
+        return moma_ctx_sync_status(self.handle)
+
+    def _out(self, like, out):
+        import torch
+        return torch.empty_like(like) if out is None else out
+
+    def addmod(self, a, b, out=None, stream=None):
+        out = self._out(a, out)
+        moma_vec_addmod(self.handle, a.shape[-1], a, b, out, stream)
+        return out
+
+    def submod(self, a, b, out=None, stream=None):
+        out = self._out(a, out)
+        moma_vec_submod(self.handle, a.shape[-1], a, b, out, stream)
+        return out
+
+    def mulmod(self, a, b, out=None, stream=None):
+        out = self._out(a, out)
+        moma_vec_mulmod(self.handle, a.shape[-1], a, b, out, stream)
+        return out
+
+    def axpy(self, alpha: int, x, y, out=None, stream=None):
+        out = self._out(x, out)
+        moma_vec_axpymod(self.handle, x.shape[-1], alpha, x, y, out, stream)
+        return out
+
+    def ntt(self, x, out=None, inverse=False, stream=None):
+        out = self._out(x, out)
+        n = x.shape[-1]
+        if x.dim() == 3:
+            (moma_ntt_inv_many if inverse else moma_ntt_fwd_many)(self.handle, n, x.shape[0], x, out, stream)
+        else:
+            (moma_ntt_inv if inverse else moma_ntt_fwd)(self.handle, n, x, out, stream)
+        return out
+
+    def intt(self, x, out=None, stream=None):
+        return self.ntt(x, out, inverse=True, stream=stream)
+
+    def polymul(self, a, b, out=None, stream=None):
+        out = self._out(a, out)
+        moma_polymul(self.handle, a.shape[-1], a, b, out, stream)
+        return out

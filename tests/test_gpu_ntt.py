@@ -1,0 +1,214 @@
+"""Parity of the forward/inverse NTT and the fused cyclic product (C ABI) with the oracle.
+
+Bit-exact everywhere (integer path).  Sizes cover the single-pass tile, every multi-pass
+split (2, 3 and 4 Stockham passes) and the largest supported size; 2^20 at 256 bits is
+compared in full, 2^24 on sampled outputs (Horner) plus the round trip and linearity,
+which hold at any size.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_07535_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+NTT_WIDTHS = [128, 256, 384]
+
+
+@pytest.fixture(scope="module")
+def ctxs(gpu):
+    out = {w: gpu.moma_ctx_create(inputs.prime(w).q, w) for w in NTT_WIDTHS}
+    yield out
+    for h in out.values():
+        gpu.moma_ctx_destroy(h)
+
+
+def test_roots_match_oracle(gpu, ctxs):
+    for w in NTT_WIDTHS:
+        q = inputs.prime(w).q
+        for lg in range(1, 25):
+            assert gpu.moma_ctx_root(ctxs[w], 1 << lg) == oracle.root_of_unity(q, 1 << lg), (w, lg)
+
+
+@pytest.mark.parametrize("width", NTT_WIDTHS)
+@pytest.mark.parametrize("lg", [1, 2, 3, 5, 8, 10, 11, 12, 13, 14, 15, 17])
+def test_ntt_parity(gpu, ctxs, width, lg):
+    p = inputs.prime(width)
+    n = 1 << lg
+    x = inputs.residues(p.q, p.L, n, seed=lg)
+    xi = inputs.to_ints(x)
+    dx = gpu.to_device(x)
+    dy = torch.empty_like(dx)
+    dz = torch.empty_like(dx)
+    gpu.moma_ntt_fwd(ctxs[width], n, dx, dy)
+    gpu.moma_ntt_inv(ctxs[width], n, dx, dz)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(xi, p.q)
+    assert inputs.to_ints(gpu.to_host(dz)) == oracle.ntt_inv(xi, p.q)
+    gpu.moma_ntt_inv(ctxs[width], n, dy, dz)
+    torch.cuda.synchronize()
+    assert torch.equal(dz, dx)
+
+
+@pytest.mark.parametrize("width", NTT_WIDTHS)
+def test_ntt_special_inputs(gpu, ctxs, width):
+    p = inputs.prime(width)
+    n = 1 << 13
+    w = oracle.root_of_unity(p.q, n)
+    for vec, expect in (([1] + [0] * (n - 1), [1] * n),
+                        ([1] * n, [n] + [0] * (n - 1)),
+                        ([0, 1] + [0] * (n - 2), [pow(w, k, p.q) for k in range(n)]),
+                        ([p.q - 1] * n, [(n * (p.q - 1)) % p.q] + [0] * (n - 1))):
+        dx = gpu.to_device(inputs.from_ints(vec, p.L))
+        dy = torch.empty_like(dx)
+        gpu.moma_ntt_fwd(ctxs[width], n, dx, dy)
+        torch.cuda.synchronize()
+        assert inputs.to_ints(gpu.to_host(dy)) == expect
+
+
+@pytest.mark.parametrize("width", [128, 256])
+@pytest.mark.parametrize("lg,count", [(9, 5), (12, 3), (14, 2)])
+def test_ntt_many(gpu, ctxs, width, lg, count):
+    p = inputs.prime(width)
+    n = 1 << lg
+    xs = [inputs.residues(p.q, p.L, n, seed=100 + t) for t in range(count)]
+    dx = gpu.to_device(np.stack(xs))
+    dy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd_many(ctxs[width], n, count, dx, dy)
+    dz = torch.empty_like(dx)
+    gpu.moma_ntt_inv_many(ctxs[width], n, count, dy, dz)
+    torch.cuda.synchronize()
+    host = gpu.to_host(dy)
+    for t in range(count):
+        assert inputs.to_ints(host[t]) == oracle.ntt_fwd(inputs.to_ints(xs[t]), p.q), t
+    assert torch.equal(dz, dx)
+
+
+@pytest.mark.parametrize("lg", [6, 11, 12, 13, 20])
+def test_ntt_in_place(gpu, ctxs, lg):
+    p = inputs.prime(256)
+    n = 1 << lg
+    x = inputs.residues(p.q, p.L, n, seed=7)
+    d = gpu.to_device(x)
+    gpu.moma_ntt_fwd(ctxs[256], n, d, d)
+    torch.cuda.synchronize()
+    got = gpu.to_host(d)
+    if lg <= 13:
+        assert inputs.to_ints(got) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
+    gpu.moma_ntt_inv(ctxs[256], n, d, d)
+    torch.cuda.synchronize()
+    assert np.array_equal(gpu.to_host(d), x)
+
+
+def test_ntt_256bit_2p20_full(gpu, ctxs):
+    """The headline size: a 2^20-point transform over the 256-bit prime, every output."""
+    p = inputs.prime(256)
+    n = 1 << 20
+    x = inputs.residues(p.q, p.L, n, seed=0)
+    dx = gpu.to_device(x)
+    dy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd(ctxs[256], n, dx, dy)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
+
+
+@pytest.mark.parametrize("width", [256, 384])
+def test_ntt_2p24_sampled_and_roundtrip(gpu, ctxs, width):
+    p = inputs.prime(width)
+    n = 1 << 24
+    x = inputs.residues(p.q, p.L, n, seed=24)
+    dx = gpu.to_device(x)
+    dy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd(ctxs[width], n, dx, dy)
+    dz = torch.empty_like(dx)
+    gpu.moma_ntt_inv(ctxs[width], n, dy, dz)
+    torch.cuda.synchronize()
+    assert torch.equal(dz, dx)
+    w = oracle.root_of_unity(p.q, n)
+    xi = inputs.to_ints(x)
+    ks = [1, 1 + int(np.random.Generator(np.random.PCG64(width)).integers(1, n - 1))]
+    got = inputs.to_ints(gpu.to_host(dy[:, torch.tensor(ks, device="cuda")]))
+    assert got == [oracle.ntt_eval_at(xi, p.q, k, w) for k in ks]
+    # linearity on the device: fwd(x + y) == fwd(x) + fwd(y)
+    y = inputs.residues(p.q, p.L, n, seed=25)
+    dyy = gpu.to_device(y)
+    s = torch.empty_like(dx)
+    gpu.moma_vec_addmod(ctxs[width], n, dx, dyy, s)
+    fs = torch.empty_like(dx)
+    gpu.moma_ntt_fwd(ctxs[width], n, s, fs)
+    fy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd(ctxs[width], n, dyy, fy)
+    gpu.moma_vec_addmod(ctxs[width], n, dy, fy, s)
+    torch.cuda.synchronize()
+    assert torch.equal(s, fs)
+
+
+@pytest.mark.parametrize("width", NTT_WIDTHS)
+@pytest.mark.parametrize("lg", [1, 6, 12, 15])
+def test_polymul_parity(gpu, ctxs, width, lg):
+    p = inputs.prime(width)
+    n = 1 << lg
+    a = inputs.residues(p.q, p.L, n, seed=31)
+    b = inputs.residues(p.q, p.L, n, seed=32)
+    ai, bi = inputs.to_ints(a), inputs.to_ints(b)
+    da, db = gpu.to_device(a), gpu.to_device(b)
+    dc = torch.empty_like(da)
+    gpu.moma_polymul(ctxs[width], n, da, db, dc)
+    torch.cuda.synchronize()
+    ref = oracle.cyclic_convolution_naive(ai, bi, p.q) if lg <= 6 else oracle.polymul_cyclic(ai, bi, p.q)
+    assert inputs.to_ints(gpu.to_host(dc)) == ref
+    gpu.moma_polymul(ctxs[width], n, da, db, da)  # output aliases an input
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(da)) == ref
+
+
+def _ctx_raw(gpu, q, bits):
+    L = bits // 32
+    arr = (ctypes.c_uint32 * L)(*inputs.int_to_limbs(q, L))
+    h = ctypes.c_void_p()
+    rc = gpu.lib().moma_ctx_create(ctypes.cast(arr, ctypes.c_void_p), bits, ctypes.byref(h))
+    return rc, h.value
+
+
+def test_ntt_argument_errors(gpu, ctxs):
+    lib = gpu.lib()
+    h = ctxs[256]
+    x = gpu.to_device(inputs.residues(inputs.prime(256).q, 8, 64, 1))
+    ptr = x.data_ptr()
+    assert lib.moma_ntt_fwd(h, 3, ptr, ptr, None) == 3            # not a power of two
+    assert lib.moma_ntt_fwd(h, 1 << 25, ptr, ptr, None) == 3      # above 2^24
+    assert lib.moma_ntt_fwd(h, 0, ptr, ptr, None) == 3
+    assert lib.moma_ntt_fwd(h, 64, None, ptr, None) == 1
+    assert lib.moma_ntt_fwd(h, 64, ptr + 2, ptr, None) == 4
+    # 768-bit transforms are not built in this version
+    c768 = gpu.moma_ctx_create(inputs.prime(768).q, 768)
+    try:
+        x768 = gpu.to_device(inputs.residues(inputs.prime(768).q, 24, 64, 1))
+        assert lib.moma_ntt_fwd(c768, 64, x768.data_ptr(), x768.data_ptr(), None) == 9
+    finally:
+        gpu.moma_ctx_destroy(c768)
+    # composite modulus of the right size: BLAS works, the transform refuses
+    q = (1 << 251) + 1
+    while oracle.is_probable_prime(q):
+        q += 2
+    rc, hc = _ctx_raw(gpu, q, 256)
+    assert rc == 0
+    try:
+        assert lib.moma_ntt_fwd(hc, 64, ptr, ptr, None) == 2
+    finally:
+        lib.moma_ctx_destroy(hc)
+    # prime with q = 3 mod 4: no 4th root of unity
+    q = (1 << 251) + 3
+    while not oracle.is_probable_prime(q):
+        q += 4
+    rc, hp = _ctx_raw(gpu, q, 256)
+    assert rc == 0
+    try:
+        assert lib.moma_ntt_fwd(hp, 2, ptr, ptr, None) == 0
+        assert lib.moma_ntt_fwd(hp, 4, ptr, ptr, None) == 3
+    finally:
+        torch.cuda.synchronize()
+        lib.moma_ctx_destroy(hp)
