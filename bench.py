@@ -93,6 +93,7 @@ def oracle_mulmod_rate(pool, cores, q, n=1 << 19):
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
+    """nvidia-smi sampling (every 20 ms) around the measured phase; waits for the first sample."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -100,27 +101,38 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
+
+    def _reader(self):
+        for ln in self.proc.stdout:
+            if ln.strip():
+                self.lines.append(ln)
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._reader, daemon=True)
+        self.thread.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 10:
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            self.thread.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -210,18 +222,17 @@ def run_ours(args):
     def ntt_step():
         moma.moma_ntt_fwd_many(ctx, n, NTT_BATCH, dx, dy)
 
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         ntt_step()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(st)
-        for _ in range(args.steps):
-            ntt_step()
-        e1.record(st)
-        barrier()
+    e0.record(st)
+    for _ in range(args.steps):
+        ntt_step()
+    e1.record(st)
+    barrier()
     ntt_ms = max_over_ranks(e0.elapsed_time(e1))
-    clocks = clk.summary()
     ntt_per_s = world * NTT_BATCH * args.steps / (ntt_ms * 1e-3)
 
     # ---- mulmod region
@@ -257,6 +268,8 @@ def run_ours(args):
     t1.record(st)
     barrier()
     e2e_ms = max_over_ranks(t0.elapsed_time(t1))
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
     e2e = world * NTT_BATCH * args.steps / (e2e_ms * 1e-3)
     step_bytes = NTT_BATCH * L * n * 4
 
@@ -326,6 +339,26 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """Small case for ncu captures: only batched forward NTTs (plan set-up call first)."""
+    import numpy as np
+    import torch
+
+    from paper_2501_07535_gb300 import build, inputs, moma
+    build.build()
+    q = inputs.prime(WIDTH).q
+    n = 1 << LOGN
+    ctx = moma.moma_ctx_create(q, WIDTH)
+    xs = np.stack([inputs.residues(q, L, n, seed=10 + t) for t in range(args.ntt_batch)])
+    dx = moma.to_device(xs)
+    dy = torch.empty_like(dx)
+    for _ in range(1 + args.steps):
+        moma.moma_ntt_fwd_many(ctx, n, args.ntt_batch, dx, dy)
+    torch.cuda.synchronize()
+    moma.moma_ctx_destroy(ctx)
+    print(json.dumps({"profile": "ntt_fwd_many", "n": n, "batch": args.ntt_batch, "calls": 1 + args.steps}))
+
+
 def _pass_count(logn, L):
     tile = {4: 12, 8: 11, 12: 11}[L]
     if logn <= tile:
@@ -379,10 +412,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="small NTT-only case for ncu captures")
+    ap.add_argument("--ntt-batch", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -135,10 +135,12 @@ moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint3
 /* ------------------------------------------------------------------ measurement */
 
 /* Integer multiply-add issue-rate microbenchmark (used for the compute roofline).
- * Runs `blocks` x `threads` threads, each issuing `iters` rounds of a fixed block of
- * mad.lo.cc / madc.hi.cc carry chains (variant 0: 8 independent chains per thread;
- * variant 1: one dependent chain).  Writes the kernel time in milliseconds and the
- * number of 32-bit multiply-add instructions it issued.  Synchronous. */
+ * Runs `blocks` x `threads` threads (threads <= 256), each issuing `iters` rounds of 64
+ * multiply instructions of one PTX form: 0 carry-chain rows (mad.lo.cc/madc.lo.cc then
+ * mad.hi.cc/madc.hi.cc, 8 independent chains), 1 the same as one dependent chain,
+ * 2 mad.lo/mad.hi alternating, 3 mad.lo only, 4 mad.hi only, 5 mad.wide.u32.  Writes the
+ * kernel time in milliseconds and the number of multiply instructions issued.
+ * Synchronous (uses the legacy default stream). */
 moma_status moma_probe_imad(int variant, int blocks, int threads, int iters, double *ms_out,
                             double *imad_out);
 
