@@ -138,8 +138,10 @@ moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint3
  * Runs `blocks` x `threads` threads (threads <= 256), each issuing `iters` rounds of 64
  * multiply instructions of one PTX form: 0 carry-chain rows (mad.lo.cc/madc.lo.cc then
  * mad.hi.cc/madc.hi.cc, 8 independent chains), 1 the same as one dependent chain,
- * 2 mad.lo/mad.hi alternating, 3 mad.lo only, 4 mad.hi only, 5 mad.wide.u32.  Writes the
- * kernel time in milliseconds and the number of multiply instructions issued.
+ * 2 mad.lo/mad.hi alternating, 3 mad.lo only, 4 mad.hi only, 5 mad.wide.u32, 6 lo
+ * carry rows only, 7 hi carry rows only, 8 add.cc chains (no multiply), 9 rows as plain
+ * 64-bit C arithmetic (64 word products).  Writes the kernel time in milliseconds and
+ * 64 * iters * blocks * threads (the operations issued at the PTX/C level).
  * Synchronous (uses the legacy default stream). */
 moma_status moma_probe_imad(int variant, int blocks, int threads, int iters, double *ms_out,
                             double *imad_out);

@@ -100,13 +100,15 @@ MOMA_DEV void static_for(F&& f) {
   }
 }
 
-// Largest power of two strictly below n (n >= 2): the low part of one recursion step.
-template <int N>
-constexpr int low_split() {
-  int p = 1;
-  while (p * 2 < N) p *= 2;
-  return p;
-}
+// Largest power of two strictly below N (N >= 2): the low part of one recursion step.
+template <int N, int P = 1, bool MORE = (P * 2 < N)>
+struct LowSplit {
+  static constexpr int value = P;
+};
+template <int N, int P>
+struct LowSplit<N, P, true> {
+  static constexpr int value = LowSplit<N, P * 2>::value;
+};
 
 // ------------------------------------------------------------------ rules (addqdd)/(adc)
 // c = a + b over N words; CIN: a carry is pending in the flag from a lower part.
@@ -115,7 +117,7 @@ MOMA_DEV void add_words(uint32_t* c, const uint32_t* a, const uint32_t* b) {
   if constexpr (N == 1) {
     c[0] = CIN ? addc_cc(a[0], b[0]) : add_cc(a[0], b[0]);
   } else {
-    constexpr int H = low_split<N>();
+    constexpr int H = LowSplit<N>::value;
     add_words<H, CIN>(c, a, b);
     add_words<N - H, true>(c + H, a + H, b + H);
   }
@@ -127,7 +129,7 @@ MOMA_DEV void sub_words(uint32_t* c, const uint32_t* a, const uint32_t* b) {
   if constexpr (N == 1) {
     c[0] = BIN ? subc_cc(a[0], b[0]) : sub_cc(a[0], b[0]);
   } else {
-    constexpr int H = low_split<N>();
+    constexpr int H = LowSplit<N>::value;
     sub_words<H, BIN>(c, a, b);
     sub_words<N - H, true>(c + H, a + H, b + H);
   }

@@ -15,6 +15,9 @@ namespace moma {
 //   2  mad.lo and mad.hi without carries, alternating
 //   3  mad.lo only            4  mad.hi only
 //   5  mad.wide.u32 (32x32 -> 64-bit product plus 64-bit addend: a whole word product)
+//   6  mad.lo.cc/madc.lo.cc rows only      7  mad.hi.cc/madc.hi.cc rows only
+//   8  add.cc/addc.cc chains (no multiply; the carry-propagation cost)
+//   9  rows written as plain 64-bit C arithmetic: t = x*y[j] + acc[j] + (t >> 32)
 template <int VARIANT>
 __global__ void __launch_bounds__(256) probe_imad_kernel(uint32_t* sink, int iters, uint32_t seed) {
   uint32_t acc[8][4];
@@ -44,6 +47,42 @@ __global__ void __launch_bounds__(256) probe_imad_kernel(uint32_t* sink, int ite
         row_lo<4, false>(acc[0], x, y);
         row_hi<4, false>(acc[0], x, y);
       }
+    } else if constexpr (VARIANT == 6 || VARIANT == 7) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t x = acc[c][3] | 1u;
+        if constexpr (VARIANT == 6) {
+          row_lo<4, false>(acc[c], x, y);
+          row_lo<4, false>(acc[c], x ^ 0x5bd1e995u, y);
+        } else {
+          row_hi<4, false>(acc[c], x, y);
+          row_hi<4, false>(acc[c], x ^ 0x5bd1e995u, y);
+        }
+      }
+    } else if constexpr (VARIANT == 8) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+          add_words<4, false>(acc[c], acc[c], acc[c + 1]);
+          add_words<4, false>(acc[c + 1], acc[c + 1], acc[c]);
+          add_words<4, false>(acc[c], acc[c], y);
+          add_words<4, false>(acc[c + 1], acc[c + 1], y);
+        }
+    } else if constexpr (VARIANT == 9) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint32_t x = acc[c][3] | 1u;
+          uint64_t t = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            t = (uint64_t)x * y[k] + acc[c][k] + (t >> 32);
+            acc[c][k] = (uint32_t)t;
+          }
+          acc[c][0] ^= (uint32_t)(t >> 32);
+        }
     } else if constexpr (VARIANT == 5) {
 #pragma unroll
       for (int r = 0; r < 8; ++r)
@@ -85,7 +124,7 @@ using namespace moma;
 
 extern "C" moma_status moma_probe_imad(int variant, int blocks, int threads, int iters, double* ms_out,
                                        double* imad_out) {
-  if (blocks <= 0 || threads <= 0 || threads > 256 || iters <= 0 || variant < 0 || variant > 5)
+  if (blocks <= 0 || threads <= 0 || threads > 256 || iters <= 0 || variant < 0 || variant > 9)
     return MOMA_ERR_INVALID_ARG;
   uint32_t* sink = nullptr;
   if (cudaMalloc(&sink, (size_t)blocks * threads * sizeof(uint32_t)) != cudaSuccess) return MOMA_ERR_OOM;
@@ -99,7 +138,11 @@ extern "C" moma_status moma_probe_imad(int variant, int blocks, int threads, int
       case 2: probe_imad_kernel<2><<<blocks, threads>>>(sink, it, 12345u); break;
       case 3: probe_imad_kernel<3><<<blocks, threads>>>(sink, it, 12345u); break;
       case 4: probe_imad_kernel<4><<<blocks, threads>>>(sink, it, 12345u); break;
-      default: probe_imad_kernel<5><<<blocks, threads>>>(sink, it, 12345u); break;
+      case 5: probe_imad_kernel<5><<<blocks, threads>>>(sink, it, 12345u); break;
+      case 6: probe_imad_kernel<6><<<blocks, threads>>>(sink, it, 12345u); break;
+      case 7: probe_imad_kernel<7><<<blocks, threads>>>(sink, it, 12345u); break;
+      case 8: probe_imad_kernel<8><<<blocks, threads>>>(sink, it, 12345u); break;
+      default: probe_imad_kernel<9><<<blocks, threads>>>(sink, it, 12345u); break;
     }
   };
   launch(iters / 8 + 1);  // warm-up
