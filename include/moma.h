@@ -132,6 +132,48 @@ moma_status moma_ntt_inv_many(moma_ctx *ctx, size_t n, size_t count, const uint3
 moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
                          uint32_t *c, void *stream);
 
+/* ------------------------------------------------------------------ kernel configuration */
+
+/* Operation codes (kernel configuration keys and batch job kinds). */
+typedef enum {
+  MOMA_OP_NTT_FWD = 0,
+  MOMA_OP_NTT_INV = 1,
+  MOMA_OP_POLYMUL = 2,
+  MOMA_OP_ADD = 3,
+  MOMA_OP_SUB = 4,
+  MOMA_OP_MUL = 5,
+  MOMA_OP_AXPY = 6
+} moma_op;
+
+/* Schedule of one operation at one size.  Any field set to 0 means "library default".
+ *   engine     1: word products as mad.lo/mad.hi carry chains (mad.lo.cc, madc.hi.cc);
+ *              2: word products as mad.wide (whole 64-bit products, carry in the addend).
+ *              Both compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd).
+ *   tile_log   transforms: log2 of the elements one CTA holds in shared memory.
+ *   max_logr   transforms: largest radix (log2) of one Stockham pass.
+ *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment). */
+typedef struct {
+  int engine;
+  int tile_log;
+  int max_logr;
+  int vec_width;
+} moma_config;
+
+/* Set / read the schedule used for `op` at size n (transforms: exact n; BLAS: every n).
+ * moma_ctx_get_config reports the effective schedule (defaults filled in).  Invalid
+ * combinations (shared memory over the limit, radix above the tile) give
+ * MOMA_ERR_INVALID_ARG. */
+moma_status moma_ctx_set_config(moma_ctx *ctx, int op, size_t n, const moma_config *cfg);
+moma_status moma_ctx_get_config(moma_ctx *ctx, int op, size_t n, moma_config *cfg);
+
+/* Autotuner: time every candidate schedule of `op` at size n (and `count` transforms for
+ * the NTT ops) on scratch buffers of the context's device, with CUDA events on `stream`,
+ * keep the fastest in the context (as if set by moma_ctx_set_config) and write it to
+ * *best (may be NULL) and its time per call in microseconds to *best_us (may be NULL).
+ * Synchronous.  Allocates and frees its scratch buffers. */
+moma_status moma_autotune(moma_ctx *ctx, int op, size_t n, size_t count, void *stream,
+                          moma_config *best, double *best_us);
+
 /* ------------------------------------------------------------------ measurement */
 
 /* Integer multiply-add issue-rate microbenchmark (used for the compute roofline).

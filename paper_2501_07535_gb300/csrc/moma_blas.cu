@@ -42,7 +42,7 @@ struct VecT<4> {
   static __device__ __forceinline__ T join(const uint32_t* o) { return make_uint4(o[0], o[1], o[2], o[3]); }
 };
 
-template <int L, int OP, int V>
+template <int L, int OP, int V, bool WIDE>
 __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArgs<L> p) {
   using VT = typename VecT<V>::T;
   const uint64_t units = p.n / V;
@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
       } else if constexpr (OP == VEC_SUB) {
         submod<L>(z[v], x[v], y[v], p.k.q);
       } else if constexpr (OP == VEC_MUL) {
-        mulmod_barrett<L>(z[v], x[v], y[v], p.k);
+        mulmod_barrett<L, WIDE>(z[v], x[v], y[v], p.k);
       } else {
         uint32_t ax[L];
-        mulmod_fixed<L>(ax, x[v], p.alpha, p.alphap, p.k);
+        mulmod_fixed<L, WIDE>(ax, x[v], p.alpha, p.alphap, p.k);
         addmod<L>(z[v], ax, y[v], p.k.q);
       }
     }
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
   }
 }
 
-template <int L, int OP, int V>
+template <int L, int OP, int V, bool WIDE>
 static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                            const uint32_t* alpha_host, cudaStream_t st) {
   VecArgs<L> p;
@@ -109,7 +109,8 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
   static int occ = -1;  // per-instantiation occupancy, computed once
   if (occ < 0) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V>, 256, 0) != cudaSuccess) return MOMA_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V, WIDE>, 256, 0) != cudaSuccess)
+      return MOMA_ERR_CUDA;
     occ = o > 0 ? o : 1;
   }
   const uint64_t units = n / V;
@@ -117,47 +118,68 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
   const uint64_t cap = (uint64_t)ctx->num_sms * (uint64_t)occ;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) return MOMA_OK;
-  vec_kernel<L, OP, V><<<(unsigned)blocks, 256, 0, st>>>(p);
+  vec_kernel<L, OP, V, WIDE><<<(unsigned)blocks, 256, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
 }
 
-// Vector width per (L, op): keep the two operand tiles (2*V*L words) near 64 registers.
-template <int L>
-constexpr int pick_v() {
-  return L <= 8 ? 4 : (L <= 12 ? 2 : 1);
+// Largest vector width per L: keeps the two operand tiles (2*V*L words) near 64 registers.
+int vec_max_width(int L) { return L <= 8 ? 4 : (L <= 12 ? 2 : 1); }
+
+moma_config vec_config(const moma_ctx* ctx, int vec_op) {
+  moma_config c = {0, 0, 0, 0};
+  auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
+  if (it != ctx->configs.end()) c = it->second;
+  if (c.engine == 0) c.engine = 1;
+  if (c.vec_width == 0) c.vec_width = vec_max_width(ctx->L);
+  c.tile_log = 0;
+  c.max_logr = 0;
+  return c;
 }
 
-template <int L, int OP>
-static moma_status dispatch_v(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b,
-                              uint32_t* c, const uint32_t* alpha, cudaStream_t st) {
-  constexpr int VB = pick_v<L>();
+template <int L, int OP, bool WIDE>
+static moma_status dispatch_v(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                              const uint32_t* alpha, int vw, cudaStream_t st) {
+  constexpr int VM = L <= 8 ? 4 : (L <= 12 ? 2 : 1);
   const uintptr_t mis = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c;
-  if (VB >= 4 && n % 4 == 0 && (mis & 15) == 0) return run_vec<L, OP, (VB >= 4 ? 4 : 1)>(ctx, n, a, b, c, alpha, st);
-  if (VB >= 2 && n % 2 == 0 && (mis & 7) == 0) return run_vec<L, OP, (VB >= 2 ? 2 : 1)>(ctx, n, a, b, c, alpha, st);
-  return run_vec<L, OP, 1>(ctx, n, a, b, c, alpha, st);
+  if (VM >= 4 && vw >= 4 && n % 4 == 0 && (mis & 15) == 0)
+    return run_vec<L, OP, (VM >= 4 ? 4 : 1), WIDE>(ctx, n, a, b, c, alpha, st);
+  if (VM >= 2 && vw >= 2 && n % 2 == 0 && (mis & 7) == 0)
+    return run_vec<L, OP, (VM >= 2 ? 2 : 1), WIDE>(ctx, n, a, b, c, alpha, st);
+  return run_vec<L, OP, 1, WIDE>(ctx, n, a, b, c, alpha, st);
 }
 
 template <int L>
-static moma_status dispatch_op(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
-                               uint32_t* c, const uint32_t* alpha, cudaStream_t st) {
+static moma_status dispatch_op(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                               const uint32_t* alpha, const moma_config& cfg, cudaStream_t st) {
+  const bool wide = cfg.engine == 2;
+  const int vw = cfg.vec_width;
   switch (op) {
-    case VEC_ADD: return dispatch_v<L, VEC_ADD>(ctx, n, a, b, c, alpha, st);
-    case VEC_SUB: return dispatch_v<L, VEC_SUB>(ctx, n, a, b, c, alpha, st);
-    case VEC_MUL: return dispatch_v<L, VEC_MUL>(ctx, n, a, b, c, alpha, st);
-    case VEC_AXPY: return dispatch_v<L, VEC_AXPY>(ctx, n, a, b, c, alpha, st);
+    case VEC_ADD: return dispatch_v<L, VEC_ADD, false>(ctx, n, a, b, c, alpha, vw, st);
+    case VEC_SUB: return dispatch_v<L, VEC_SUB, false>(ctx, n, a, b, c, alpha, vw, st);
+    case VEC_MUL:
+      return wide ? dispatch_v<L, VEC_MUL, true>(ctx, n, a, b, c, alpha, vw, st)
+                  : dispatch_v<L, VEC_MUL, false>(ctx, n, a, b, c, alpha, vw, st);
+    case VEC_AXPY:
+      return wide ? dispatch_v<L, VEC_AXPY, true>(ctx, n, a, b, c, alpha, vw, st)
+                  : dispatch_v<L, VEC_AXPY, false>(ctx, n, a, b, c, alpha, vw, st);
   }
   return MOMA_ERR_INVALID_ARG;
 }
 
-moma_status launch_vec(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
-                       uint32_t* c, const uint32_t* alpha_host, cudaStream_t st) {
+moma_status launch_vec_cfg(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                           const uint32_t* alpha_host, const moma_config& cfg, cudaStream_t st) {
   switch (ctx->L) {
-    case 4: return dispatch_op<4>(ctx, op, n, a, b, c, alpha_host, st);
-    case 8: return dispatch_op<8>(ctx, op, n, a, b, c, alpha_host, st);
-    case 12: return dispatch_op<12>(ctx, op, n, a, b, c, alpha_host, st);
-    case 24: return dispatch_op<24>(ctx, op, n, a, b, c, alpha_host, st);
+    case 4: return dispatch_op<4>(ctx, op, n, a, b, c, alpha_host, cfg, st);
+    case 8: return dispatch_op<8>(ctx, op, n, a, b, c, alpha_host, cfg, st);
+    case 12: return dispatch_op<12>(ctx, op, n, a, b, c, alpha_host, cfg, st);
+    case 24: return dispatch_op<24>(ctx, op, n, a, b, c, alpha_host, cfg, st);
   }
   return MOMA_ERR_INVALID_ARG;
+}
+
+moma_status launch_vec(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                       const uint32_t* alpha_host, cudaStream_t st) {
+  return launch_vec_cfg(ctx, op, n, a, b, c, alpha_host, vec_config(ctx, op), st);
 }
 
 }  // namespace moma

@@ -5,6 +5,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -35,6 +36,7 @@ struct PassDesc {
 struct Plan {
   int logn = 0;
   bool inverse = false;
+  int max_logr = 0;
   std::vector<PassDesc> passes;
   uint32_t* d_tables = nullptr;  // one allocation holding every table of the plan
   uint32_t scale[kMaxL] = {}, scalep[kMaxL] = {};  // n^-1 and its companion (inverse)
@@ -56,8 +58,11 @@ struct moma_ctx {
   int ntt_ready = 0;  // 0: not yet, 1: ok, -1: modulus not prime
   uint32_t g = 0;     // smallest quadratic non-residue
   int two_adicity = 0;
-  std::map<std::pair<int, int>, moma::Plan*> plans;  // (logn, inverse) -> plan
-  int* d_status = nullptr;                            // device-side error word
+  // (logn, inverse, tile_log, max_logr) -> plan
+  std::map<std::tuple<int, int, int, int>, moma::Plan*> plans;
+  // schedule per (op, logn) for transforms, (op, -1) for BLAS; absent = defaults
+  std::map<std::pair<int, int>, moma_config> configs;
+  int* d_status = nullptr;  // device-side error word
 };
 
 namespace moma {
@@ -67,16 +72,28 @@ inline moma_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MOMA_O
 
 // moma_blas.cu
 enum VecOp { VEC_ADD = 0, VEC_SUB = 1, VEC_MUL = 2, VEC_AXPY = 3 };
+int vec_max_width(int L);
+moma_config vec_config(const moma_ctx* ctx, int vec_op);  // effective (defaults filled)
 moma_status launch_vec(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
                        uint32_t* c, const uint32_t* alpha_host, cudaStream_t st);
+moma_status launch_vec_cfg(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
+                           uint32_t* c, const uint32_t* alpha_host, const moma_config& cfg, cudaStream_t st);
 
 // moma_ntt.cu
+int default_tile_log(int L);
+int max_tile_log(int L);                 // shared-memory limit
+moma_config ntt_config(const moma_ctx* ctx, int op, int logn);  // effective (defaults filled)
+bool ntt_config_valid(int L, int logn, const moma_config& c);
 moma_status ntt_prepare(moma_ctx* ctx);  // primality, generator (takes ctx->lock)
-moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, Plan** out);
+moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out);
 moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in,
                        uint32_t* out, cudaStream_t st);
+moma_status launch_ntt_cfg(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in,
+                           uint32_t* out, const moma_config& cfg, cudaStream_t st);
 moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
                            uint32_t* c, cudaStream_t st);
+moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
+                               uint32_t* c, const moma_config& cfg, cudaStream_t st);
 void free_plan(Plan* p);
 BigU root_of_unity(moma_ctx* ctx, int logn);  // requires ntt_prepare()
 

@@ -80,6 +80,10 @@ MOMA_DEV uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) { return a * b + c;
 MOMA_DEV uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) { return __umulhi(a, b) + c; }
 // (hi:lo) >> s for 0 <= s < 32
 MOMA_DEV uint32_t shr_pair(uint32_t lo, uint32_t hi, uint32_t s) { return __funnelshift_r(lo, hi, s); }
+// whole word product plus a 64-bit addend: a*b + c < 2^64 whenever c < 2^33
+MOMA_DEV uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t r; asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c)); return r;
+}
 #endif
 
 // Carry (0/1) left in the flag by the last chain.
@@ -251,6 +255,74 @@ MOMA_DEV void mul_hi_trunc(uint32_t (&H)[L], const uint32_t (&x)[L], const uint3
   for (int k = 0; k < L; ++k) H[k] = A[k + 1];
 }
 
+// ------------------------------------------------------------------ wide-product rows
+// The same schoolbook sums as above, with each word product formed whole by mad.wide
+// (one 32x32->64 multiply) and the running carry of the row passed through the 64-bit
+// addend: t = x*y[j] + acc[j] + c, acc[j] = lo(t), c = hi(t).  On GB300 a whole product
+// costs 4 multiply-pipe cycles per warp this way, against ~6 for a mad.lo.cc/madc.hi.cc pair.
+
+// acc[0..N) += x*y[0..N) + cin; returns the carry out of acc[N-1].
+template <int N>
+MOMA_DEV uint32_t roww(uint32_t* acc, uint32_t x, const uint32_t* y, uint32_t cin) {
+  uint32_t c = cin;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const uint64_t t = mad_wide(x, y[j], (uint64_t)acc[j] + c);
+    acc[j] = (uint32_t)t;
+    c = (uint32_t)(t >> 32);
+  }
+  return c;
+}
+
+// t[0..2L) = x * y.
+template <int L>
+MOMA_DEV void mul_full_w(uint32_t (&t)[2 * L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const uint64_t w = mad_wide(x[0], y[j], (uint64_t)c);
+    t[j] = (uint32_t)w;
+    c = (uint32_t)(w >> 32);
+  }
+  t[L] = c;
+#pragma unroll
+  for (int i = 1; i < L; ++i) t[i + L] = roww<L>(t + i, x[i], y, 0u);
+}
+
+// r = r + x * y mod 2^(32L).  Row i: whole products below the top word, then one low
+// multiply-add for the top word (its carry is not needed).
+template <int L>
+MOMA_DEV void mul_lo_acc_w(uint32_t (&r)[L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  static_for<0, L>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    uint32_t c = 0;
+    if constexpr (L - 1 - i > 0) c = roww<L - 1 - i>(r + i, x[i], y, 0u);
+    r[L - 1] = x[i] * y[L - 1 - i] + r[L - 1] + c;
+  });
+}
+
+// Same quotient estimate as mul_hi_trunc (columns >= L-1 plus the high halves of column L-2).
+// Row i starts at j0 = L-2-i: that product only contributes its high word, as carry into
+// word L-1; A[p] holds word L-1+p.
+template <int L>
+MOMA_DEV void mul_hi_trunc_w(uint32_t (&H)[L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  uint32_t A[L + 1];
+#pragma unroll
+  for (int p = 0; p <= L; ++p) A[p] = 0u;
+  static_for<0, L>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    if constexpr (i < L - 1) {
+      // j0 = L-2-i: high word only; then j = L-1-i .. L-1 land on p = 0 .. i
+      const uint64_t t0 = mad_wide(x[i], y[L - 2 - i], 0ull);
+      A[i + 1] = roww<i + 1>(A, x[i], y + (L - 1 - i), (uint32_t)(t0 >> 32));
+    } else {
+      A[L] = roww<L>(A, x[i], y, 0u);
+    }
+  });
+#pragma unroll
+  for (int k = 0; k < L; ++k) H[k] = A[k + 1];
+}
+
 // ------------------------------------------------------------------ per-modulus constants
 // Kernel-parameter copy of the constants of one modulus (lives in the constant bank).
 template <int L>
@@ -271,20 +343,22 @@ struct ModK {
 // The high half of t1*mu comes from mul_hi_trunc; its error (< L*2^-32 of one unit after
 // the shift) keeps c below 2q, so one correction suffices as in Listing 1.
 // Returns the quotient estimate s in `s` (callers that need floor(t/q) add the correction).
-template <int L>
+template <int L, bool WIDE = false>
 MOMA_DEV uint32_t barrett_reduce(uint32_t (&c)[L], uint32_t (&s)[L], const uint32_t (&t)[2 * L],
                                  const ModK<L>& k) {
   uint32_t t1[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) t1[i] = shr_pair(t[L - 1 + i], t[L + i], 26u);
   uint32_t h[L];
-  mul_hi_trunc<L>(h, t1, k.mu);
+  if constexpr (WIDE) mul_hi_trunc_w<L>(h, t1, k.mu);
+  else mul_hi_trunc<L>(h, t1, k.mu);
 #pragma unroll
   for (int i = 0; i < L - 1; ++i) s[i] = shr_pair(h[i], h[i + 1], 1u);
   s[L - 1] = h[L - 1] >> 1;
 #pragma unroll
   for (int i = 0; i < L; ++i) c[i] = t[i];
-  mul_lo_acc<L>(c, s, k.nq);
+  if constexpr (WIDE) mul_lo_acc_w<L>(c, s, k.nq);
+  else mul_lo_acc<L>(c, s, k.nq);
   // final correction (the conditional subtraction of Listing 1); report whether it fired
   uint32_t d[L];
   sub_words<L, false>(d, c, k.q);
@@ -294,14 +368,15 @@ MOMA_DEV uint32_t barrett_reduce(uint32_t (&c)[L], uint32_t (&s)[L], const uint3
   return ~keep & 1u;
 }
 
-// c = a * b mod q (Eq. barrett).
-template <int L>
+// c = a * b mod q (Eq. barrett).  WIDE selects the whole-product rows.
+template <int L, bool WIDE = false>
 MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
                              const ModK<L>& k) {
   uint32_t t[2 * L];
-  mul_full<L>(t, a, b);
+  if constexpr (WIDE) mul_full_w<L>(t, a, b);
+  else mul_full<L>(t, a, b);
   uint32_t s[L];
-  barrett_reduce<L>(c, s, t, k);
+  barrett_reduce<L, WIDE>(c, s, t, k);
 }
 
 // ------------------------------------------------------------------ fixed multiplicand
@@ -311,22 +386,28 @@ MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uin
 //   s = floor(a*wp / 2^(32L)) (truncated, exact or one less);  r = a*w - s*q mod 2^(32L).
 // For any a < 2^(32L): a*w/q - s < 3, so r lies in [0, 3q), which fits the container.
 // Used for twiddle factors (tables carry the companion) and for the axpy scalar.
-template <int L>
+template <int L, bool WIDE = false>
 MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
                                 const uint32_t (&wp)[L], const ModK<L>& k) {
   uint32_t s[L];
-  mul_hi_trunc<L>(s, a, wp);
 #pragma unroll
   for (int i = 0; i < L; ++i) r[i] = 0u;
-  mul_lo_acc<L>(r, a, w);
-  mul_lo_acc<L>(r, s, k.nq);
+  if constexpr (WIDE) {
+    mul_hi_trunc_w<L>(s, a, wp);
+    mul_lo_acc_w<L>(r, a, w);
+    mul_lo_acc_w<L>(r, s, k.nq);
+  } else {
+    mul_hi_trunc<L>(s, a, wp);
+    mul_lo_acc<L>(r, a, w);
+    mul_lo_acc<L>(r, s, k.nq);
+  }
 }
 
 // Canonical form: r in [0, 3q) -> [0, q).
-template <int L>
+template <int L, bool WIDE = false>
 MOMA_DEV void mulmod_fixed(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
                            const uint32_t (&wp)[L], const ModK<L>& k) {
-  mulmod_fixed_lazy<L>(r, a, w, wp, k);
+  mulmod_fixed_lazy<L, WIDE>(r, a, w, wp, k);
   cond_sub<L>(r, k.q2);  // [0,3q) -> [0,2q)
   cond_sub<L>(r, k.q);   // -> [0,q)
 }

@@ -27,14 +27,42 @@ namespace moma {
 
 constexpr int kNttThreads = 256;
 
-// Largest CTA tile (elements) per width: the tile takes L*T*4 bytes of shared memory.
-static int tile_log_for(int L) {
+// Default CTA tile (elements) per width: the tile takes L*T*4 bytes of shared memory.
+int default_tile_log(int L) {
   switch (L) {
     case 4: return 12;   // 64 KiB
     case 8: return 11;   // 64 KiB
     case 12: return 11;  // 96 KiB
     default: return 10;
   }
+}
+
+// Largest tile that fits the 227 KiB of shared memory one CTA may use.
+int max_tile_log(int L) {
+  int t = 5;
+  while ((size_t)L * 4u << (t + 1) <= 227u * 1024u) ++t;
+  return t;
+}
+
+constexpr int kDefaultEngine = 1;
+
+moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
+  moma_config c = {0, 0, 0, 0};
+  auto it = ctx->configs.find(std::make_pair(op, logn));
+  if (it != ctx->configs.end()) c = it->second;
+  if (c.engine == 0) c.engine = kDefaultEngine;
+  if (c.tile_log == 0) c.tile_log = default_tile_log(ctx->L);
+  if (c.max_logr == 0) c.max_logr = c.tile_log > 6 ? c.tile_log - 5 : 1;
+  c.vec_width = 0;
+  return c;
+}
+
+bool ntt_config_valid(int L, int logn, const moma_config& c) {
+  (void)logn;
+  if (c.engine < 0 || c.engine > 2) return false;
+  if (c.tile_log != 0 && (c.tile_log < 5 || c.tile_log > max_tile_log(L))) return false;
+  if (c.max_logr < 0 || (c.max_logr != 0 && c.tile_log != 0 && c.max_logr > c.tile_log)) return false;
+  return true;
 }
 
 // XOR swizzle of a word index inside one limb plane of the tile: flips the low five
@@ -60,7 +88,7 @@ struct NttPassArgs {
 
 enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4 };
 
-template <int L>
+template <int L, bool WIDE>
 __global__ void __launch_bounds__(kNttThreads) ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ uint32_t sm[];
   const uint32_t R = 1u << p.logR;
@@ -86,13 +114,13 @@ __global__ void __launch_bounds__(kNttThreads) ntt_pass_kernel(const __grid_cons
       uint32_t u[L], t[L];
 #pragma unroll
       for (int l = 0; l < L; ++l) u[l] = p.src2[idx + (uint64_t)l * p.n];
-      mulmod_barrett<L>(t, v, u, p.k);
+      mulmod_barrett<L, WIDE>(t, v, u, p.k);
 #pragma unroll
       for (int l = 0; l < L; ++l) v[l] = t[l];
     }
     if (p.flags & F_SCALE) {
       uint32_t t[L];
-      mulmod_fixed<L>(t, v, p.sc, p.scp, p.k);
+      mulmod_fixed<L, WIDE>(t, v, p.sc, p.scp, p.k);
 #pragma unroll
       for (int l = 0; l < L; ++l) v[l] = t[l];
     }
@@ -104,7 +132,7 @@ __global__ void __launch_bounds__(kNttThreads) ntt_pass_kernel(const __grid_cons
         w[l] = __ldg(p.tw_pass + ti + (uint64_t)l * p.tw_count);
         wp[l] = __ldg(p.tw_pass + ti + (uint64_t)(L + l) * p.tw_count);
       }
-      mulmod_fixed<L>(t, v, w, wp, p.k);
+      mulmod_fixed<L, WIDE>(t, v, w, wp, p.k);
 #pragma unroll
       for (int l = 0; l < L; ++l) v[l] = t[l];
     }
@@ -141,7 +169,7 @@ __global__ void __launch_bounds__(kNttThreads) ntt_pass_kernel(const __grid_cons
           w[l] = __ldg(p.tw_int + ti + l * half_int);
           wp[l] = __ldg(p.tw_int + ti + (L + l) * half_int);
         }
-        mulmod_fixed<L>(y1, d, w, wp, p.k);
+        mulmod_fixed<L, WIDE>(y1, d, w, wp, p.k);
 #pragma unroll
         for (int l = 0; l < L; ++l) d[l] = y1[l];
       }
@@ -308,18 +336,19 @@ static void split_passes(int logn, int max_logr, std::vector<int>& out) {
   for (int i = 0; i < P; ++i) out.push_back(logn / P + (i < logn % P ? 1 : 0));
 }
 
-static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, Plan** out) {
+static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out) {
   const int L = ctx->L;
   Plan* pl = new Plan();
   pl->logn = logn;
   pl->inverse = inverse;
-  pl->tile_log = tile_log_for(L);
+  pl->tile_log = tile_log;
+  pl->max_logr = max_logr;
   const int T = pl->tile_log;
   std::vector<int> radices;
   if (logn <= T) {
     radices.push_back(logn);
   } else {
-    split_passes(logn, T - 5, radices);  // at least 32 groups per tile
+    split_passes(logn, max_logr, radices);
   }
   BigU w = root_of_unity(ctx, logn);
   if (inverse) w = ctx->red->powmod(w, sub(pow2(logn), BigU(1)));  // w^(n-1) = w^-1
@@ -378,26 +407,27 @@ static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, Plan** out)
   return MOMA_OK;
 }
 
-moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, Plan** out) {
+moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out) {
   moma_status st = ntt_prepare(ctx);
   if (st) return st;
   if (logn > ctx->two_adicity || logn < 1 || logn > kMaxLogN) return MOMA_ERR_SIZE;
+  if (logn <= tile_log) max_logr = 0;  // single pass: the split does not matter
   std::lock_guard<std::mutex> g(ctx->lock);
-  auto key = std::make_pair(logn, inverse ? 1 : 0);
+  auto key = std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     *out = it->second;
     return MOMA_OK;
   }
   Plan* pl = nullptr;
-  st = build_plan(ctx, logn, inverse, &pl);
+  st = build_plan(ctx, logn, inverse, tile_log, max_logr, &pl);
   if (st) return st;
   ctx->plans[key] = pl;
   *out = pl;
   return MOMA_OK;
 }
 
-template <int L>
+template <int L, bool WIDE>
 static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
                             const uint32_t* src2, uint32_t* dst, uint32_t flags, cudaStream_t st) {
   NttPassArgs<L> a;
@@ -421,24 +451,28 @@ static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, si
   const size_t smem = (size_t)L * 4u << (d.logR + d.logG);
   static bool attr_done = false;
   if (!attr_done) {
-    if (cudaFuncSetAttribute(ntt_pass_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             L * 4 << tile_log_for(L)) != cudaSuccess)
+    if (cudaFuncSetAttribute(ntt_pass_kernel<L, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             L * 4 << max_tile_log(L)) != cudaSuccess)
       return MOMA_ERR_CUDA;
     attr_done = true;
   }
   const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
   if (grid == 0) return MOMA_OK;
   if (grid > 0x7fffffffull) return MOMA_ERR_SIZE;
-  ntt_pass_kernel<L><<<(unsigned)grid, kNttThreads, smem, st>>>(a);
+  ntt_pass_kernel<L, WIDE><<<(unsigned)grid, kNttThreads, smem, st>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
 static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
-                              const uint32_t* src2, uint32_t* dst, uint32_t flags, cudaStream_t st) {
+                              const uint32_t* src2, uint32_t* dst, uint32_t flags, int engine, cudaStream_t st) {
+  const bool wide = engine == 2;
   switch (ctx->L) {
-    case 4: return run_pass<4>(ctx, pl, d, count, src, src2, dst, flags, st);
-    case 8: return run_pass<8>(ctx, pl, d, count, src, src2, dst, flags, st);
-    case 12: return run_pass<12>(ctx, pl, d, count, src, src2, dst, flags, st);
+    case 4: return wide ? run_pass<4, true>(ctx, pl, d, count, src, src2, dst, flags, st)
+                        : run_pass<4, false>(ctx, pl, d, count, src, src2, dst, flags, st);
+    case 8: return wide ? run_pass<8, true>(ctx, pl, d, count, src, src2, dst, flags, st)
+                        : run_pass<8, false>(ctx, pl, d, count, src, src2, dst, flags, st);
+    case 12: return wide ? run_pass<12, true>(ctx, pl, d, count, src, src2, dst, flags, st)
+                         : run_pass<12, false>(ctx, pl, d, count, src, src2, dst, flags, st);
   }
   return MOMA_ERR_UNSUPPORTED;
 }
@@ -446,7 +480,7 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
 // Run every pass of a plan: in -> [scratch1 -> scratch2 -> ...] -> out.  The first pass can
 // fuse a pointwise product with src2 (polymul) and, for the inverse, the n^-1 scaling.
 static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
-                            uint32_t* out, cudaStream_t st) {
+                            uint32_t* out, int engine, cudaStream_t st) {
   const size_t P = pl->passes.size();
   const size_t words = (size_t)ctx->L * ((size_t)1 << pl->logn) * count;
   uint32_t* s1 = nullptr;
@@ -463,7 +497,7 @@ static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const u
     uint32_t flags = 0;
     if (i == 0 && in2) flags |= F_POINTWISE;
     if (i == 0 && pl->inverse) flags |= F_SCALE;
-    rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, st);
+    rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, engine, st);
     src = dst;
   }
   if (s1) cudaFreeAsync(s1, st);
@@ -471,31 +505,42 @@ static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const u
   return rc;
 }
 
-moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in, uint32_t* out,
-                       cudaStream_t st) {
+moma_status launch_ntt_cfg(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in, uint32_t* out,
+                           const moma_config& cfg, cudaStream_t st) {
   Plan* pl = nullptr;
-  moma_status rc = get_plan(ctx, logn, inverse, &pl);
+  moma_status rc = get_plan(ctx, logn, inverse, cfg.tile_log, cfg.max_logr, &pl);
   if (rc) return rc;
   if (count == 0) return MOMA_OK;
-  return run_plan(ctx, pl, count, in, nullptr, out, st);
+  return run_plan(ctx, pl, count, in, nullptr, out, cfg.engine, st);
 }
 
-moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b, uint32_t* c,
-                           cudaStream_t st) {
+moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in, uint32_t* out,
+                       cudaStream_t st) {
+  return launch_ntt_cfg(ctx, logn, count, inverse, in, out,
+                        ntt_config(ctx, inverse ? MOMA_OP_NTT_INV : MOMA_OP_NTT_FWD, logn), st);
+}
+
+moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                               const moma_config& cfg, cudaStream_t st) {
   Plan *fw = nullptr, *iv = nullptr;
-  moma_status rc = get_plan(ctx, logn, false, &fw);
+  moma_status rc = get_plan(ctx, logn, false, cfg.tile_log, cfg.max_logr, &fw);
   if (rc) return rc;
-  rc = get_plan(ctx, logn, true, &iv);
+  rc = get_plan(ctx, logn, true, cfg.tile_log, cfg.max_logr, &iv);
   if (rc) return rc;
   const size_t words = (size_t)ctx->L << logn;
   uint32_t* fa = nullptr;
   if (cudaMallocAsync(&fa, 2 * words * 4, st) != cudaSuccess) return MOMA_ERR_OOM;
   uint32_t* fb = fa + words;
-  rc = run_plan(ctx, fw, 1, a, nullptr, fa, st);
-  if (!rc) rc = run_plan(ctx, fw, 1, b, nullptr, fb, st);
-  if (!rc) rc = run_plan(ctx, iv, 1, fa, fb, c, st);
+  rc = run_plan(ctx, fw, 1, a, nullptr, fa, cfg.engine, st);
+  if (!rc) rc = run_plan(ctx, fw, 1, b, nullptr, fb, cfg.engine, st);
+  if (!rc) rc = run_plan(ctx, iv, 1, fa, fb, c, cfg.engine, st);
   cudaFreeAsync(fa, st);
   return rc;
+}
+
+moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                           cudaStream_t st) {
+  return launch_polymul_cfg(ctx, logn, a, b, c, ntt_config(ctx, MOMA_OP_POLYMUL, logn), st);
 }
 
 }  // namespace moma

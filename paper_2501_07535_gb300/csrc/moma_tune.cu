@@ -1,0 +1,164 @@
+// moma_tune.cu -- per-context kernel schedules and the autotuner.
+//
+// A schedule (moma_config) picks the word-product form of the multi-word multiplication
+// (carry chains or whole mad.wide products), the shared-memory tile of the transform and
+// the largest radix of one Stockham pass, and the vector width of the BLAS kernels.  Every
+// schedule computes bit-identical results; only speed differs.  The autotuner times each
+// candidate with CUDA events on the caller's stream and keeps the fastest.
+#include <vector>
+
+#include "moma_internal.hpp"
+
+using namespace moma;
+
+static bool is_ntt_op(int op) { return op == MOMA_OP_NTT_FWD || op == MOMA_OP_NTT_INV || op == MOMA_OP_POLYMUL; }
+static bool is_vec_op(int op) { return op >= MOMA_OP_ADD && op <= MOMA_OP_AXPY; }
+
+static int log2_of(size_t n) {
+  if (n == 0 || (n & (n - 1))) return -1;
+  int k = 0;
+  while (((size_t)1 << k) < n) ++k;
+  return k;
+}
+
+extern "C" moma_status moma_ctx_set_config(moma_ctx* ctx, int op, size_t n, const moma_config* cfg) {
+  if (!ctx || !cfg) return MOMA_ERR_INVALID_ARG;
+  if (is_ntt_op(op)) {
+    const int lg = log2_of(n);
+    if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
+    if (!ntt_config_valid(ctx->L, lg, *cfg)) return MOMA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->lock);
+    ctx->configs[std::make_pair(op, lg)] = *cfg;
+    return MOMA_OK;
+  }
+  if (is_vec_op(op)) {
+    if (cfg->engine < 0 || cfg->engine > 2) return MOMA_ERR_INVALID_ARG;
+    if (cfg->vec_width != 0 && cfg->vec_width != 1 && cfg->vec_width != 2 && cfg->vec_width != 4)
+      return MOMA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->lock);
+    ctx->configs[std::make_pair(op, -1)] = *cfg;
+    return MOMA_OK;
+  }
+  return MOMA_ERR_INVALID_ARG;
+}
+
+extern "C" moma_status moma_ctx_get_config(moma_ctx* ctx, int op, size_t n, moma_config* cfg) {
+  if (!ctx || !cfg) return MOMA_ERR_INVALID_ARG;
+  if (is_ntt_op(op)) {
+    const int lg = log2_of(n);
+    if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
+    std::lock_guard<std::mutex> g(ctx->lock);
+    *cfg = ntt_config(ctx, op, lg);
+    return MOMA_OK;
+  }
+  if (is_vec_op(op)) {
+    std::lock_guard<std::mutex> g(ctx->lock);
+    *cfg = vec_config(ctx, op - MOMA_OP_ADD);
+    return MOMA_OK;
+  }
+  return MOMA_ERR_INVALID_ARG;
+}
+
+namespace {
+
+struct Scratch {
+  std::vector<uint32_t*> bufs;
+  ~Scratch() {
+    for (auto* p : bufs) cudaFree(p);
+  }
+  uint32_t* get(size_t words, cudaStream_t st) {
+    uint32_t* p = nullptr;
+    if (cudaMalloc(&p, words * 4) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    // 0x01010101 in every limb: canonical for every supported modulus (top limb < q's)
+    cudaMemsetAsync(p, 0x01, words * 4, st);
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t count, void* stream, moma_config* best,
+                                     double* best_us) {
+  if (!ctx) return MOMA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<moma_config> cands;
+  int lg = -1;
+  if (is_ntt_op(op)) {
+    if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
+    lg = log2_of(n);
+    if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
+    if (count == 0) count = 1;
+    if (op == MOMA_OP_POLYMUL) count = 1;
+    const int t0 = default_tile_log(ctx->L);
+    for (int engine = 1; engine <= 2; ++engine)
+      for (int t = t0 - 1; t <= t0 + 1; ++t) {
+        if (t < 5 || t > max_tile_log(ctx->L)) continue;
+        if (lg <= t) {
+          cands.push_back({engine, t, t, 0});
+          continue;
+        }
+        for (int r = t - 3; r >= t - 5; --r)
+          if (r >= 1) cands.push_back({engine, t, r, 0});
+      }
+  } else if (is_vec_op(op)) {
+    if (n == 0) return MOMA_ERR_SIZE;
+    const bool mul = op == MOMA_OP_MUL || op == MOMA_OP_AXPY;
+    for (int engine = 1; engine <= (mul ? 2 : 1); ++engine)
+      for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v});
+  } else {
+    return MOMA_ERR_INVALID_ARG;
+  }
+
+  Scratch sc;
+  const size_t words = (size_t)ctx->L * n * (count ? count : 1);
+  uint32_t* a = sc.get(words, st);
+  uint32_t* b = sc.get(words, st);
+  uint32_t* c = sc.get(words, st);
+  if (!a || !b || !c) return MOMA_ERR_OOM;
+  std::vector<uint32_t> alpha(ctx->L, 0x01010101u);
+
+  auto run = [&](const moma_config& cfg) -> moma_status {
+    switch (op) {
+      case MOMA_OP_NTT_FWD: return launch_ntt_cfg(ctx, lg, count, false, a, c, cfg, st);
+      case MOMA_OP_NTT_INV: return launch_ntt_cfg(ctx, lg, count, true, a, c, cfg, st);
+      case MOMA_OP_POLYMUL: return launch_polymul_cfg(ctx, lg, a, b, c, cfg, st);
+      default: return launch_vec_cfg(ctx, op - MOMA_OP_ADD, n, a, b, c, alpha.data(), cfg, st);
+    }
+  };
+
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MOMA_ERR_CUDA;
+  double best_t = 1e30;
+  moma_config best_c = cands.empty() ? moma_config{0, 0, 0, 0} : cands[0];
+  moma_status rc = MOMA_OK;
+  for (const auto& cfg : cands) {
+    rc = run(cfg);  // first use builds the plan (twiddle tables) outside the timing
+    if (rc) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MOMA_ERR_CUDA; break; }
+    double t_cfg = 1e30;
+    for (int round = 0; round < 2 && rc == MOMA_OK; ++round) {
+      const int reps = 3;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == MOMA_OK; ++r) rc = run(cfg);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = MOMA_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t_cfg = std::min(t_cfg, 1e3 * ms / reps);
+    }
+    if (rc) break;
+    if (t_cfg < best_t) {
+      best_t = t_cfg;
+      best_c = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = moma_ctx_set_config(ctx, op, n, &best_c);
+  if (rc) return rc;
+  if (best) *best = best_c;
+  if (best_us) *best_us = best_t;
+  return MOMA_OK;
+}

@@ -55,7 +55,20 @@ _SIGS = {
     "moma_polymul": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
     "moma_probe_imad": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "moma_ctx_set_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
+    "moma_ctx_get_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
+    "moma_autotune": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _SZ, _P, _P, ctypes.POINTER(ctypes.c_double)]),
 }
+
+OPS = {"ntt_fwd": 0, "ntt_inv": 1, "polymul": 2, "add": 3, "sub": 4, "mul": 5, "axpy": 6}
+
+
+class moma_config(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int), ("tile_log", ctypes.c_int), ("max_logr", ctypes.c_int),
+                ("vec_width", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 def lib() -> ctypes.CDLL:
@@ -185,6 +198,30 @@ def moma_probe_imad(variant: int, blocks: int, threads: int, iters: int):
     _check(lib().moma_probe_imad(variant, blocks, threads, iters, ctypes.byref(ms), ctypes.byref(cnt)),
            "moma_probe_imad")
     return ms.value, cnt.value
+
+
+def _op(op) -> int:
+    return OPS[op] if isinstance(op, str) else int(op)
+
+
+def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0):
+    cfg = moma_config(engine, tile_log, max_logr, vec_width)
+    _check(lib().moma_ctx_set_config(ctx, _op(op), n, ctypes.byref(cfg)), "moma_ctx_set_config")
+
+
+def moma_ctx_get_config(ctx, op, n) -> dict:
+    cfg = moma_config()
+    _check(lib().moma_ctx_get_config(ctx, _op(op), n, ctypes.byref(cfg)), "moma_ctx_get_config")
+    return cfg.as_dict()
+
+
+def moma_autotune(ctx, op, n, count=1, stream=None):
+    """Time every candidate schedule of `op` at size n; the context keeps the fastest."""
+    cfg = moma_config()
+    us = ctypes.c_double()
+    _check(lib().moma_autotune(ctx, _op(op), n, count, _stream_handle(stream), ctypes.byref(cfg),
+                               ctypes.byref(us)), "moma_autotune")
+    return cfg.as_dict(), us.value
 
 
 # ----------------------------------------------------------------- conveniences

@@ -1,0 +1,103 @@
+"""Kernel schedules (product engine, tile, radix split, vector width) and the autotuner.
+
+Every schedule must give bit-identical results; the autotuner's choice is checked the
+same way against the oracle.
+"""
+import pytest
+import torch
+
+import oracle
+from paper_2501_07535_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("width", [128, 256, 384])
+@pytest.mark.parametrize("engine", [1, 2])
+def test_ntt_every_engine_and_split(gpu, width, engine):
+    p = inputs.prime(width)
+    ctx = gpu.moma_ctx_create(p.q, width)
+    try:
+        for lg, tile, rmax in ((10, 11, 6), (13, 10, 5), (13, 11, 8), (15, 12, 7)):
+            if tile > 12 and p.L == 12:
+                continue
+            n = 1 << lg
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, engine=engine, tile_log=tile, max_logr=rmax)
+            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, engine=engine, tile_log=tile, max_logr=rmax)
+            cfg = gpu.moma_ctx_get_config(ctx, "ntt_fwd", n)
+            assert (cfg["engine"], cfg["tile_log"], cfg["max_logr"]) == (engine, tile, rmax)
+            x = inputs.residues(p.q, p.L, n, seed=lg + engine)
+            dx = gpu.to_device(x)
+            dy = torch.empty_like(dx)
+            gpu.moma_ntt_fwd(ctx, n, dx, dy)
+            dz = torch.empty_like(dx)
+            gpu.moma_ntt_inv(ctx, n, dy, dz)
+            torch.cuda.synchronize()
+            assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q), (lg, tile, rmax)
+            assert torch.equal(dz, dx)
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("width", [128, 256, 384, 768])
+@pytest.mark.parametrize("engine", [1, 2])
+def test_blas_every_engine_and_width(gpu, width, engine):
+    p = inputs.prime(width)
+    ctx = gpu.moma_ctx_create(p.q, width)
+    try:
+        n = 4096 + 4
+        a = inputs.residues(p.q, p.L, n, 1)
+        b = inputs.residues(p.q, p.L, n, 2)
+        ai, bi = inputs.to_ints(a), inputs.to_ints(b)
+        alpha = inputs.scalar_residue(p.q, 5)
+        da, db = gpu.to_device(a), gpu.to_device(b)
+        for vw in (1, 2, 4):
+            for op in ("mul", "axpy"):
+                gpu.moma_ctx_set_config(ctx, op, n, engine=engine, vec_width=vw)
+            dc = torch.empty_like(da)
+            gpu.moma_vec_mulmod(ctx, n, da, db, dc)
+            torch.cuda.synchronize()
+            assert inputs.to_ints(gpu.to_host(dc)) == oracle.vec_mulmod(ai, bi, p.q), vw
+            gpu.moma_vec_axpymod(ctx, n, alpha, da, db, dc)
+            torch.cuda.synchronize()
+            assert inputs.to_ints(gpu.to_host(dc)) == oracle.vec_axpy(alpha, ai, bi, p.q), vw
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
+def test_autotune_ntt_and_mul(gpu):
+    p = inputs.prime(256)
+    ctx = gpu.moma_ctx_create(p.q, 256)
+    try:
+        n = 1 << 14
+        best, us = gpu.moma_autotune(ctx, "ntt_fwd", n, 4)
+        assert best["engine"] in (1, 2) and us > 0
+        assert gpu.moma_ctx_get_config(ctx, "ntt_fwd", n) == best
+        x = inputs.residues(p.q, p.L, n, 3)
+        dx = gpu.to_device(x)
+        dy = torch.empty_like(dx)
+        gpu.moma_ntt_fwd(ctx, n, dx, dy)
+        torch.cuda.synchronize()
+        assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
+        best, us = gpu.moma_autotune(ctx, "mul", 1 << 16)
+        assert best["vec_width"] in (1, 2, 4) and us > 0
+        best, us = gpu.moma_autotune(ctx, "polymul", 1 << 12)
+        assert us > 0
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
+def test_config_rejects_invalid(gpu):
+    p = inputs.prime(256)
+    ctx = gpu.moma_ctx_create(p.q, 256)
+    try:
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", 1 << 10, tile_log=30)
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", 1 << 10, engine=7)
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(ctx, "mul", 1 << 10, vec_width=3)
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(ctx, 99, 1 << 10)
+    finally:
+        gpu.moma_ctx_destroy(ctx)
