@@ -132,6 +132,26 @@ moma_status moma_ntt_inv_many(moma_ctx *ctx, size_t n, size_t count, const uint3
 moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
                          uint32_t *c, void *stream);
 
+/* Same result as moma_ntt_fwd (one transform), but the call allocates no device memory:
+ * its intermediate buffers are a fixed 8 MiB array inside the library, held by every GPU
+ * that loads it until the process exits.  Meant for callers that may not allocate device
+ * memory at call time (memory owned by another allocator under a fixed budget, or a hot
+ * path that must not wait on an allocator).  The paper has no counterpart; this is an
+ * interface convenience of this library.
+ * Limits and conditions:
+ *   - L*n <= 2^20 words (n <= 2^18 at 128 bits, 2^17 at 256, 2^16 at 384); larger n gives
+ *     MOMA_ERR_SIZE.  768-bit contexts give MOMA_ERR_UNSUPPORTED.
+ *   - The size's twiddle tables must already exist: call moma_ntt_fwd once with this
+ *     context and n beforehand (that call allocates); otherwise MOMA_ERR_INVALID_ARG.
+ *   - The context's device must be current.  The first call on a device looks up the
+ *     array's device address (no allocation); make that first call before any stream
+ *     capture that should contain this entry point.
+ *   - All calls share the one array.  Each call writes every word it later reads, so
+ *     nothing needs clearing between calls, but calls that overlap on the GPU (other
+ *     streams, other host threads, other contexts) race on it and give wrong results. */
+moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, uint32_t *out,
+                                 void *stream);
+
 /* ------------------------------------------------------------------ kernel configuration */
 
 /* Operation codes (kernel configuration keys and batch job kinds). */

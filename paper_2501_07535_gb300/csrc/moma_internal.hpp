@@ -95,6 +95,12 @@ moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uin
 moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
                                uint32_t* c, const moma_config& cfg, cudaStream_t st);
 void free_plan(Plan* p);
+// Existing plan or null; never builds one (no allocation).
+Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr);
+// All passes of an existing single-transform plan with caller-provided scratch
+// (s1: passes 0, 2, ...; s2: passes 1, 3, ...; each L*n words; unused ones may be null).
+moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out, int engine,
+                             uint32_t* s1, uint32_t* s2, cudaStream_t st);
 BigU root_of_unity(moma_ctx* ctx, int logn);  // requires ntt_prepare()
 
 // Shoup-style companion floor(w * 2^(32L) / q) for a host constant w < q.

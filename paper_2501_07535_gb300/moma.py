@@ -58,6 +58,7 @@ _SIGS = {
     "moma_ctx_set_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
     "moma_ctx_get_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
     "moma_autotune": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _SZ, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "moma_ntt_fwd_noalloc": (ctypes.c_int, [_P, _SZ, _P, _P, _P]),
 }
 
 OPS = {"ntt_fwd": 0, "ntt_inv": 1, "polymul": 2, "add": 3, "sub": 4, "mul": 5, "axpy": 6}
@@ -186,6 +187,14 @@ def moma_ntt_fwd_many(ctx, n, count, x, y, stream=None):
 
 def moma_ntt_inv_many(ctx, n, count, x, y, stream=None):
     _check(lib().moma_ntt_inv_many(ctx, n, count, _ptr(x), _ptr(y), _stream_handle(stream)), "moma_ntt_inv_many")
+
+
+def moma_ntt_fwd_noalloc(ctx, n, x, y, stream=None):
+    """Forward NTT without device allocation (scratch in a fixed array of the library).
+
+    For callers that may not allocate device memory at call time.  n*L <= 2^20; call
+    moma_ntt_fwd once for this context and n first (it builds the twiddle tables)."""
+    _check(lib().moma_ntt_fwd_noalloc(ctx, n, _ptr(x), _ptr(y), _stream_handle(stream)), "moma_ntt_fwd_noalloc")
 
 
 def moma_polymul(ctx, n, a, b, c, stream=None):
