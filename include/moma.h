@@ -152,6 +152,56 @@ moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint3
 moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, uint32_t *out,
                                  void *stream);
 
+/* ------------------------------------------------------------------ batches */
+
+/* One job of a batch.  op: MOMA_OP_NTT_FWD / NTT_INV (a -> out), MOMA_OP_POLYMUL
+ * (out = a * b mod (x^n - 1, q)), MOMA_OP_ADD / SUB / MUL (out = a op b), MOMA_OP_AXPY
+ * (out = alpha * a + b, alpha a HOST array of L limbs).  Device vectors follow the
+ * conventions above; each job uses its own context (any widths and moduli may be mixed;
+ * transforms at 128 to 384 bits, vector ops at every width). */
+typedef struct {
+  int op;
+  moma_ctx *ctx;
+  size_t n;
+  const uint32_t *a;
+  const uint32_t *b;
+  uint32_t *out;
+  const uint32_t *alpha;
+} moma_job;
+
+typedef struct moma_batch moma_batch;
+
+/* Prepare a batch (Sec. 5.1: many kernels at once).  Builds the twiddle tables the
+ * transforms need, allocates the intermediate buffers, and lays the work out as tiles for
+ * one persistent launch: a grid of resident CTAs takes tiles (one pass of one transform,
+ * or a slice of one vector op) in dependency order from a device counter; the pointwise
+ * product of a cyclic product is fused into the first pass of its inverse.  Job pointers
+ * are fixed at creation; refill the same input buffers between runs.  Synchronous. */
+moma_status moma_batch_create(const moma_job *jobs, int njobs, moma_batch **out);
+
+/* Run the batch on `stream` (asynchronous).  On a non-default stream the first run
+ * captures the launch sequence in a CUDA graph and later runs replay it; on the legacy
+ * default stream, or while the caller is capturing, it launches directly. */
+moma_status moma_batch_run(moma_batch *batch, void *stream);
+
+/* Wait for the device, then return and clear the batch's device-side status:
+ * MOMA_ERR_TIMEOUT if a dependency wait ran out (results of the skipped tiles are
+ * undefined), else MOMA_OK. */
+moma_status moma_batch_sync_status(moma_batch *batch);
+
+/* Bound of every dependency wait, in polls of about 0.1-0.2 us (default 2^24).  A wait
+ * that runs out records MOMA_ERR_TIMEOUT and the tile is skipped; the kernel never hangs. */
+moma_status moma_batch_set_wait_limit(moma_batch *batch, uint64_t polls);
+
+/* Test hook: make the last queued tile group wait for a completion that never happens,
+ * to exercise the bounded wait (the next run reports MOMA_ERR_TIMEOUT). */
+moma_status moma_batch_inject_missing_dependency(moma_batch *batch);
+
+void moma_batch_destroy(moma_batch *batch);
+
+/* create + run on `stream` + wait + destroy; returns the device-side status. */
+moma_status moma_batch_submit(const moma_job *jobs, int njobs, void *stream);
+
 /* ------------------------------------------------------------------ kernel configuration */
 
 /* Operation codes (kernel configuration keys and batch job kinds). */
@@ -171,12 +221,15 @@ typedef enum {
  *              Both compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd).
  *   tile_log   transforms: log2 of the elements one CTA holds in shared memory.
  *   max_logr   transforms: largest radix (log2) of one Stockham pass.
- *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment). */
+ *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment).
+ *   cta_threads transforms: threads per CTA (32, 64, 128 or 256).  Each CTA owns one tile;
+ *              small CTAs synchronise fewer warps between butterfly stages. */
 typedef struct {
   int engine;
   int tile_log;
   int max_logr;
   int vec_width;
+  int cta_threads;
 } moma_config;
 
 /* Set / read the schedule used for `op` at size n (transforms: exact n; BLAS: every n).

@@ -49,12 +49,14 @@ moma_status moma_ctx_create(const uint32_t* q, int bits, moma_ctx** out) {
   BigU mu;
   divmod(pow2(2 * B + 3), Q, &mu, nullptr);  // Eq. mu with k = 2B+3
   BigU q2 = add(Q, Q);
+  BigU q4 = add(q2, q2);
   BigU Q0, R0;
   divmod(W, Q, &Q0, &R0);
   Q.to_words(c->k.q, L);
   nq.to_words(c->k.nq, L);
   mu.to_words(c->k.mu, L);
   q2.to_words(c->k.q2, L);
+  q4.to_words(c->k.q4, L);
   R0.to_words(c->k.R0, L);
   c->k.Q0 = Q0.word(0);
   if (cudaGetDevice(&c->device) != cudaSuccess ||

@@ -1,0 +1,539 @@
+// moma_batch.cu -- many transforms, cyclic products and vector ops of uneven sizes and mixed
+// widths in one persistent launch.
+//
+// The paper runs many kernels concurrently by batching them (Sec. 5.1, "batch processing").
+// Here a batch is decomposed into work tiles: one CTA tile of one Stockham pass of one
+// transform (ntt_tile), or 2048 elements of one vector op.  Every tile belongs to a segment
+// (one pass of one transform, or one vector op); segments are queued by level (the pass
+// index, counting the forward passes of a cyclic product before its inverse) and a resident
+// grid of CTAs takes tiles in queue order from a global counter.  A tile of pass p waits until
+// every tile of pass p-1 of the same transform has finished (per-transform completion counters,
+// release/acquire); the inverse of a cyclic product waits for both forward transforms.  Because
+// a tile only waits for tiles that come earlier in the queue, and those were taken by CTAs that
+// are resident and running, every wait ends.  Each wait is still bounded: past the limit the
+// kernel records MOMA_ERR_TIMEOUT and skips the tile.
+//
+// Widths are mixed inside one launch: the CTA dispatches on the tile's limb count.  Products
+// use whole mad.wide rows up to 256 bits and carry chains at 384 bits (the faster form of each
+// width on GB300); results are identical either way.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "moma_internal.hpp"
+#include "moma_limbs.cuh"
+#include "moma_ntt_tile.cuh"
+
+namespace moma {
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchTileLog = 10;       // transform tiles of 2^10 elements
+constexpr uint32_t kVecTile = 2048;     // elements per vector-op tile
+constexpr uint64_t kDefaultWaitPolls = 1ull << 24;
+
+enum : uint32_t { SEG_NTT = 0, SEG_VEC = 1 };
+
+template <int L>
+struct VecJobArgs {
+  const uint32_t* a;
+  const uint32_t* b;
+  uint32_t* c;
+  uint64_t n;
+  uint32_t op;  // VecOp
+  uint32_t alpha[L], alphap[L];
+  ModK<L> k;
+};
+
+struct Seg {
+  uint32_t kind, L;
+  uint32_t first;   // first global tile of the segment
+  uint32_t ntiles;
+  uint32_t done_id;  // completion counter incremented by each tile
+  uint32_t wait_id[2];
+  uint32_t wait_count[2];  // wait until counter[wait_id] >= wait_count (0: no wait)
+  const void* args;        // device copy of NttPassArgs<L> or VecJobArgs<L>
+};
+
+template <int L>
+__device__ __forceinline__ void vec_tile(const VecJobArgs<L>& p, uint32_t tile) {
+  const uint64_t begin = (uint64_t)tile * kVecTile;
+  const uint64_t end = begin + kVecTile < p.n ? begin + kVecTile : p.n;
+  for (uint64_t e = begin + threadIdx.x; e < end; e += blockDim.x) {
+    uint32_t x[L], y[L], z[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      x[l] = __ldcg(p.a + e + (uint64_t)l * p.n);
+      y[l] = __ldcg(p.b + e + (uint64_t)l * p.n);
+    }
+    switch (p.op) {
+      case VEC_ADD: addmod<L>(z, x, y, p.k.q); break;
+      case VEC_SUB: submod<L>(z, x, y, p.k.q); break;
+      case VEC_MUL: mulmod_barrett<L, false>(z, x, y, p.k); break;
+      default: {
+        uint32_t ax[L];
+        mulmod_fixed<L, false>(ax, x, p.alpha, p.alphap, p.k);
+        addmod<L>(z, ax, y, p.k.q);
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) p.c[e + (uint64_t)l * p.n] = z[l];
+  }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __restrict__ segs, uint32_t nseg,
+                                                             uint32_t total, uint32_t* ctr, int* status,
+                                                             uint64_t wait_polls) {
+  extern __shared__ uint32_t sm[];
+  __shared__ uint32_t s_tile, s_seg, s_skip;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(&ctr[0], 1u);
+      s_tile = t;
+      s_skip = 0;
+      if (t < total) {
+        uint32_t lo = 0, hi = nseg - 1;  // last segment with first <= t
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (segs[mid].first <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        s_seg = lo;
+        const Seg& sg = segs[lo];
+        for (int w = 0; w < 2; ++w) {
+          if (sg.wait_count[w] == 0) continue;
+          uint64_t polls = 0;
+          while (ld_acquire(&ctr[1 + sg.wait_id[w]]) < sg.wait_count[w]) {
+            if (++polls > wait_polls) {
+              atomicExch(status, (int)MOMA_ERR_TIMEOUT);
+              s_skip = 1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= total) return;
+    const Seg sg = segs[s_seg];
+    if (!s_skip) {
+      const uint32_t local = t - sg.first;
+      if (sg.kind == SEG_NTT) {
+        switch (sg.L) {
+          case 4: ntt_tile<4, true>(*static_cast<const NttPassArgs<4>*>(sg.args), local, sm); break;
+          case 8: ntt_tile<8, true>(*static_cast<const NttPassArgs<8>*>(sg.args), local, sm); break;
+          case 12: ntt_tile<12, false>(*static_cast<const NttPassArgs<12>*>(sg.args), local, sm); break;
+        }
+      } else {
+        switch (sg.L) {
+          case 4: vec_tile<4>(*static_cast<const VecJobArgs<4>*>(sg.args), local); break;
+          case 8: vec_tile<8>(*static_cast<const VecJobArgs<8>*>(sg.args), local); break;
+          case 12: vec_tile<12>(*static_cast<const VecJobArgs<12>*>(sg.args), local); break;
+          case 24: vec_tile<24>(*static_cast<const VecJobArgs<24>*>(sg.args), local); break;
+        }
+      }
+    }
+    __syncthreads();  // every store of the tile is issued
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&ctr[1 + sg.done_id], 1u);
+    }
+  }
+}
+
+}  // namespace moma
+
+using namespace moma;
+
+struct moma_batch {
+  int device = 0;
+  std::vector<Seg> segs;
+  uint32_t total = 0;
+  uint32_t ncounters = 0;
+  size_t smem = 0;
+  int grid = 0;
+  uint64_t wait_polls = kDefaultWaitPolls;
+  Seg* d_segs = nullptr;
+  uint8_t* d_args = nullptr;
+  uint32_t* d_ctr = nullptr;
+  int* d_status = nullptr;
+  uint32_t* d_scratch = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool dirty = false;  // descriptors changed since upload
+};
+
+namespace {
+
+struct ArgBuf {
+  std::vector<uint8_t> bytes;
+  template <typename T>
+  size_t put(const T& v) {
+    size_t off = (bytes.size() + 15) & ~(size_t)15;
+    bytes.resize(off + sizeof(T));
+    memcpy(bytes.data() + off, &v, sizeof(T));
+    return off;
+  }
+};
+
+struct PendingSeg {
+  int level, job, sub;
+  Seg s;
+  size_t arg_off;
+};
+
+template <int L>
+void ntt_pass_args(const moma_ctx* ctx, const Plan* pl, size_t pass, const uint32_t* src, const uint32_t* src2,
+                   uint32_t* dst, uint32_t flags, ArgBuf& ab, size_t* off, uint32_t* ntiles) {
+  NttPassArgs<L> a;
+  fill_pass_args<L>(ctx, pl, pl->passes[pass], 1, src, src2, dst, flags, a);
+  *ntiles = a.tiles_per_transform;
+  *off = ab.put(a);
+}
+
+template <int L>
+size_t vec_args(const moma_ctx* ctx, const moma_job& j, ArgBuf& ab) {
+  VecJobArgs<L> a;
+  a.a = j.a;
+  a.b = j.b;
+  a.c = j.out;
+  a.n = j.n;
+  a.op = (uint32_t)(j.op - MOMA_OP_ADD);
+  for (int i = 0; i < L; ++i) {
+    a.k.q[i] = ctx->k.q[i];
+    a.k.nq[i] = ctx->k.nq[i];
+    a.k.mu[i] = ctx->k.mu[i];
+    a.k.q2[i] = ctx->k.q2[i];
+    a.k.q4[i] = ctx->k.q4[i];
+    a.alpha[i] = 0;
+    a.alphap[i] = 0;
+  }
+  if (j.op == MOMA_OP_AXPY) {
+    BigU al = BigU::from_words(j.alpha, L);
+    al.to_words(a.alpha, L);
+    companion(ctx, al, a.alphap);
+  }
+  return ab.put(a);
+}
+
+moma_status pass_args_l(const moma_ctx* ctx, const Plan* pl, size_t pass, const uint32_t* src, const uint32_t* src2,
+                        uint32_t* dst, uint32_t flags, ArgBuf& ab, size_t* off, uint32_t* ntiles) {
+  switch (ctx->L) {
+    case 4: ntt_pass_args<4>(ctx, pl, pass, src, src2, dst, flags, ab, off, ntiles); return MOMA_OK;
+    case 8: ntt_pass_args<8>(ctx, pl, pass, src, src2, dst, flags, ab, off, ntiles); return MOMA_OK;
+    case 12: ntt_pass_args<12>(ctx, pl, pass, src, src2, dst, flags, ab, off, ntiles); return MOMA_OK;
+  }
+  return MOMA_ERR_UNSUPPORTED;
+}
+
+int log2_n(size_t n) {
+  if (n == 0 || (n & (n - 1))) return -1;
+  int k = 0;
+  while (((size_t)1 << k) < n) ++k;
+  return k;
+}
+
+// Appends the segments of one transform (sub-job `sub` of job `job`) to `out`.
+moma_status add_transform(const moma_ctx* ctx, const Plan* pl, int job, int sub, int level0, uint32_t counter,
+                          const uint32_t* in, const uint32_t* in2, uint32_t* out, uint32_t* s1, uint32_t* s2,
+                          const uint32_t wait_ids[2], const uint32_t wait_counts[2], ArgBuf& ab,
+                          std::vector<PendingSeg>& segs, uint32_t* total_tiles) {
+  const size_t P = pl->passes.size();
+  const uint32_t* src = in;
+  uint32_t before = 0;
+  for (size_t i = 0; i < P; ++i) {
+    uint32_t* dst = (i + 1 == P) ? out : ((i % 2 == 0) ? s1 : s2);
+    uint32_t flags = (i + 1 == P) ? F_LAST : 0;
+    if (i == 0 && in2) flags |= F_POINTWISE;
+    if (i == 0 && pl->inverse) flags |= F_SCALE;
+    PendingSeg ps;
+    ps.level = level0 + (int)i;
+    ps.job = job;
+    ps.sub = sub;
+    ps.s = Seg{};
+    ps.s.kind = SEG_NTT;
+    ps.s.L = (uint32_t)ctx->L;
+    ps.s.done_id = counter;
+    uint32_t nt = 0;
+    moma_status rc = pass_args_l(ctx, pl, i, src, i == 0 ? in2 : nullptr, dst, flags, ab, &ps.arg_off, &nt);
+    if (rc) return rc;
+    ps.s.ntiles = nt;
+    if (i == 0) {
+      for (int w = 0; w < 2; ++w) {
+        ps.s.wait_id[w] = wait_ids[w];
+        ps.s.wait_count[w] = wait_counts[w];
+      }
+    } else {
+      ps.s.wait_id[0] = counter;
+      ps.s.wait_count[0] = before;
+    }
+    before += nt;
+    segs.push_back(ps);
+    src = dst;
+  }
+  *total_tiles = before;
+  return MOMA_OK;
+}
+
+}  // namespace
+
+extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_batch** out) {
+  if (!out) return MOMA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!jobs || njobs <= 0) return MOMA_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MOMA_ERR_CUDA;
+
+  // validate and size the scratch
+  size_t scratch_words = 0;
+  std::vector<size_t> scratch_off(njobs, 0);
+  std::vector<const Plan*> fwd(njobs, nullptr), inv(njobs, nullptr);
+  for (int j = 0; j < njobs; ++j) {
+    const moma_job& jb = jobs[j];
+    moma_ctx* ctx = jb.ctx;
+    if (!ctx || !jb.a || !jb.out) return MOMA_ERR_INVALID_ARG;
+    if (ctx->device != dev) return MOMA_ERR_INVALID_ARG;
+    const bool ntt = jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV || jb.op == MOMA_OP_POLYMUL;
+    if (!ntt && (jb.op < MOMA_OP_ADD || jb.op > MOMA_OP_AXPY)) return MOMA_ERR_INVALID_ARG;
+    if ((jb.op == MOMA_OP_POLYMUL || (!ntt)) && !jb.b) return MOMA_ERR_INVALID_ARG;
+    if (jb.op == MOMA_OP_AXPY && !jb.alpha) return MOMA_ERR_INVALID_ARG;
+    if (((uintptr_t)jb.a | (uintptr_t)jb.out | (uintptr_t)jb.b) & 3u) return MOMA_ERR_ALIGN;
+    if (!ntt) {
+      if (jb.n == 0) return MOMA_ERR_SIZE;
+      if (jb.op == MOMA_OP_AXPY && cmp(BigU::from_words(jb.alpha, ctx->L), ctx->Q) >= 0) return MOMA_ERR_INVALID_ARG;
+      continue;
+    }
+    const int lg = log2_n(jb.n);
+    if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
+    if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
+    moma_config cfg = ntt_config(ctx, jb.op, lg);
+    const int tl = std::min(cfg.tile_log, kBatchTileLog);
+    const int rmax = std::min(cfg.max_logr, tl);
+    Plan* pl = nullptr;
+    moma_status rc;
+    if (jb.op != MOMA_OP_NTT_INV) {
+      rc = get_plan(ctx, lg, false, tl, rmax, &pl);
+      if (rc) return rc;
+      fwd[j] = pl;
+    }
+    if (jb.op != MOMA_OP_NTT_FWD) {
+      rc = get_plan(ctx, lg, true, tl, rmax, &pl);
+      if (rc) return rc;
+      inv[j] = pl;
+    }
+    const size_t w = (size_t)ctx->L * jb.n;
+    scratch_off[j] = scratch_words;
+    // transforms: two ping-pong buffers; cyclic product: two more for the forward outputs
+    scratch_words += (jb.op == MOMA_OP_POLYMUL ? 6 : 2) * w;
+    scratch_words = (scratch_words + 63) & ~(size_t)63;
+  }
+
+  moma_batch* b = new (std::nothrow) moma_batch();
+  if (!b) return MOMA_ERR_OOM;
+  b->device = dev;
+  if (scratch_words && cudaMalloc(&b->d_scratch, scratch_words * 4) != cudaSuccess) {
+    delete b;
+    return MOMA_ERR_OOM;
+  }
+
+  ArgBuf ab;
+  std::vector<PendingSeg> pend;
+  uint32_t counter = 0;
+  moma_status rc = MOMA_OK;
+  for (int j = 0; j < njobs && rc == MOMA_OK; ++j) {
+    const moma_job& jb = jobs[j];
+    moma_ctx* ctx = jb.ctx;
+    const uint32_t no_id[2] = {0, 0}, no_cnt[2] = {0, 0};
+    uint32_t* base = b->d_scratch + scratch_off[j];
+    const size_t w = (size_t)ctx->L * jb.n;
+    if (jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV) {
+      const Plan* pl = jb.op == MOMA_OP_NTT_FWD ? fwd[j] : inv[j];
+      uint32_t tiles = 0;
+      rc = add_transform(ctx, pl, j, 0, 0, counter++, jb.a, nullptr, jb.out, base, base + w, no_id, no_cnt, ab, pend,
+                         &tiles);
+    } else if (jb.op == MOMA_OP_POLYMUL) {
+      uint32_t* fa = base + 2 * w;
+      uint32_t* fb = base + 3 * w;
+      const uint32_t ca = counter++, cb = counter++, cc = counter++;
+      uint32_t ta = 0, tb = 0, tc = 0;
+      rc = add_transform(ctx, fwd[j], j, 0, 0, ca, jb.a, nullptr, fa, base, base + w, no_id, no_cnt, ab, pend, &ta);
+      if (!rc)
+        rc = add_transform(ctx, fwd[j], j, 1, 0, cb, jb.b, nullptr, fb, base + 4 * w, base + 5 * w, no_id, no_cnt,
+                           ab, pend, &tb);
+      if (!rc) {
+        const uint32_t ids[2] = {ca, cb}, cnts[2] = {ta, tb};
+        rc = add_transform(ctx, inv[j], j, 2, (int)fwd[j]->passes.size(), cc, fa, fb, jb.out, base, base + w, ids,
+                           cnts, ab, pend, &tc);
+      }
+    } else {
+      PendingSeg ps;
+      ps.level = 0;
+      ps.job = j;
+      ps.sub = 0;
+      ps.s = Seg{};
+      ps.s.kind = SEG_VEC;
+      ps.s.L = (uint32_t)ctx->L;
+      ps.s.done_id = counter++;
+      ps.s.ntiles = (uint32_t)((jb.n + kVecTile - 1) / kVecTile);
+      switch (ctx->L) {
+        case 4: ps.arg_off = vec_args<4>(ctx, jb, ab); break;
+        case 8: ps.arg_off = vec_args<8>(ctx, jb, ab); break;
+        case 12: ps.arg_off = vec_args<12>(ctx, jb, ab); break;
+        default: ps.arg_off = vec_args<24>(ctx, jb, ab); break;
+      }
+      pend.push_back(ps);
+    }
+  }
+  if (rc) {
+    moma_batch_destroy(b);
+    return rc;
+  }
+  // queue order: level, then job, then sub-transform
+  std::stable_sort(pend.begin(), pend.end(), [](const PendingSeg& x, const PendingSeg& y) {
+    return std::make_tuple(x.level, x.job, x.sub) < std::make_tuple(y.level, y.job, y.sub);
+  });
+  if (cudaMalloc(&b->d_args, std::max<size_t>(ab.bytes.size(), 16)) != cudaSuccess ||
+      cudaMalloc(&b->d_segs, pend.size() * sizeof(Seg)) != cudaSuccess ||
+      cudaMalloc(&b->d_ctr, (1 + counter) * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+    moma_batch_destroy(b);
+    return MOMA_ERR_OOM;
+  }
+  uint64_t total = 0;
+  for (auto& ps : pend) {
+    ps.s.first = (uint32_t)total;
+    ps.s.args = b->d_args + ps.arg_off;
+    total += ps.s.ntiles;
+    b->segs.push_back(ps.s);
+  }
+  if (total >= 0xffffffffull) {
+    moma_batch_destroy(b);
+    return MOMA_ERR_SIZE;
+  }
+  b->total = (uint32_t)total;
+  b->ncounters = counter;
+  if (cudaMemcpy(b->d_args, ab.bytes.data(), ab.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
+    moma_batch_destroy(b);
+    return MOMA_ERR_CUDA;
+  }
+  // shared memory: the largest transform tile of the batch
+  size_t smem = 0;
+  for (int j = 0; j < njobs; ++j)
+    if (jobs[j].op <= MOMA_OP_POLYMUL) smem = std::max(smem, (size_t)jobs[j].ctx->L * 4u << kBatchTileLog);
+  b->smem = smem;
+  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(12 * 4 << kBatchTileLog)) !=
+      cudaSuccess) {
+    moma_batch_destroy(b);
+    return MOMA_ERR_CUDA;
+  }
+  int occ = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ <= 0) {
+    moma_batch_destroy(b);
+    return MOMA_ERR_CUDA;
+  }
+  b->grid = occ * sms;  // every CTA resident at once: the waits rely on it
+  *out = b;
+  return MOMA_OK;
+}
+
+static moma_status batch_launch(moma_batch* b, cudaStream_t st) {
+  if (cudaMemsetAsync(b->d_ctr, 0, (1 + b->ncounters) * sizeof(uint32_t), st) != cudaSuccess) return MOMA_ERR_CUDA;
+  batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_segs, (uint32_t)b->segs.size(), b->total, b->d_ctr,
+                                                        b->d_status, b->wait_polls);
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" moma_status moma_batch_run(moma_batch* b, void* stream) {
+  if (!b) return MOMA_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->dirty) {
+    if (cudaMemcpyAsync(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return MOMA_ERR_CUDA;
+    b->dirty = false;
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (st == nullptr || cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return batch_launch(b, st);  // legacy stream, or already inside the caller's capture
+  if (!b->graph) {
+    // capture the counter reset and the persistent launch once, replay it afterwards
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MOMA_ERR_CUDA;
+    moma_status rc = batch_launch(b, st);
+    if (cudaStreamEndCapture(st, &g) != cudaSuccess || rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc ? rc : MOMA_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return MOMA_ERR_CUDA;
+    b->graph = ex;
+  }
+  return cuda_status(cudaGraphLaunch(b->graph, st));
+}
+
+extern "C" moma_status moma_batch_sync_status(moma_batch* b) {
+  if (!b) return MOMA_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MOMA_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MOMA_ERR_CUDA;
+  if (v) cudaMemset(b->d_status, 0, sizeof(int));
+  return (moma_status)v;
+}
+
+extern "C" moma_status moma_batch_set_wait_limit(moma_batch* b, uint64_t polls) {
+  if (!b || polls == 0) return MOMA_ERR_INVALID_ARG;
+  b->wait_polls = polls;
+  if (b->graph) {  // the limit is a launch argument: capture again on the next run
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return MOMA_OK;
+}
+
+extern "C" moma_status moma_batch_inject_missing_dependency(moma_batch* b) {
+  if (!b || b->segs.empty()) return MOMA_ERR_INVALID_ARG;
+  Seg& last = b->segs.back();
+  last.wait_id[1] = last.done_id;  // waits for more of its own tiles than will ever finish
+  last.wait_count[1] = 0xffffffffu;
+  b->dirty = true;
+  return MOMA_OK;
+}
+
+extern "C" void moma_batch_destroy(moma_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->d_segs) cudaFree(b->d_segs);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_ctr) cudaFree(b->d_ctr);
+  if (b->d_status) cudaFree(b->d_status);
+  if (b->d_scratch) cudaFree(b->d_scratch);
+  delete b;
+}
+
+extern "C" moma_status moma_batch_submit(const moma_job* jobs, int njobs, void* stream) {
+  moma_batch* b = nullptr;
+  moma_status rc = moma_batch_create(jobs, njobs, &b);
+  if (rc) return rc;
+  rc = batch_launch(b, (cudaStream_t)stream);
+  if (!rc && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = MOMA_ERR_CUDA;
+  if (!rc) rc = moma_batch_sync_status(b);
+  moma_batch_destroy(b);
+  return rc;
+}

@@ -97,6 +97,7 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
     p.k.nq[i] = ctx->k.nq[i];
     p.k.mu[i] = ctx->k.mu[i];
     p.k.q2[i] = ctx->k.q2[i];
+    p.k.q4[i] = ctx->k.q4[i];
     p.alpha[i] = 0;
     p.alphap[i] = 0;
   }
@@ -126,11 +127,17 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
 int vec_max_width(int L) { return L <= 8 ? 4 : (L <= 12 ? 2 : 1); }
 
 moma_config vec_config(const moma_ctx* ctx, int vec_op) {
-  moma_config c = {0, 0, 0, 0};
+  moma_config c = {0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
   if (it != ctx->configs.end()) c = it->second;
   if (c.engine == 0) c.engine = 1;
-  if (c.vec_width == 0) c.vec_width = vec_max_width(ctx->L);
+  // measured on GB300 at 2^24 elements: multiplications prefer one element per thread from
+  // 256 bits up, additions and axpy two; narrow widths take the widest vectors
+  if (c.vec_width == 0) {
+    const int vm = vec_max_width(ctx->L);
+    const int pref = ctx->L <= 4 ? 4 : (vec_op == VEC_MUL ? 1 : 2);
+    c.vec_width = pref < vm ? pref : vm;
+  }
   c.tile_log = 0;
   c.max_logr = 0;
   return c;

@@ -20,7 +20,7 @@ constexpr int kMaxLogN = 24;
 // Host copy of the per-modulus constants (device code receives ModK<L> by value).
 struct HostConsts {
   int L = 0;
-  uint32_t q[kMaxL] = {}, nq[kMaxL] = {}, mu[kMaxL] = {}, q2[kMaxL] = {};
+  uint32_t q[kMaxL] = {}, nq[kMaxL] = {}, mu[kMaxL] = {}, q2[kMaxL] = {}, q4[kMaxL] = {};
   uint32_t R0[kMaxL] = {};  // 2^(32L) mod q
   uint32_t Q0 = 0;          // floor(2^(32L) / q)  (between 16 and 31)
 };
@@ -99,8 +99,8 @@ void free_plan(Plan* p);
 Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr);
 // All passes of an existing single-transform plan with caller-provided scratch
 // (s1: passes 0, 2, ...; s2: passes 1, 3, ...; each L*n words; unused ones may be null).
-moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out, int engine,
-                             uint32_t* s1, uint32_t* s2, cudaStream_t st);
+moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out,
+                             const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st);
 BigU root_of_unity(moma_ctx* ctx, int logn);  // requires ntt_prepare()
 
 // Shoup-style companion floor(w * 2^(32L) / q) for a host constant w < q.

@@ -331,6 +331,7 @@ struct ModK {
   uint32_t nq[L];   // 2^(32L) - q, so that  t - s*q = t + s*nq  mod 2^(32L)
   uint32_t mu[L];   // Barrett constant floor(2^(2B+3) / q)  (Eq. mu, k = 2B+3)
   uint32_t q2[L];   // 2q
+  uint32_t q4[L];   // 4q: bound of the lazy (not fully reduced) values inside a transform
 };
 
 // ------------------------------------------------------------------ Sec. 3.1, Eq. barrett

@@ -60,5 +60,5 @@ extern "C" moma_status moma_ntt_fwd_noalloc(moma_ctx* ctx, size_t n, const uint3
   uint32_t* scratch = nullptr;
   moma_status rc = noalloc_scratch(dev, &scratch);
   if (rc) return rc;
-  return run_plan_scratch(ctx, pl, in, out, cfg.engine, scratch, scratch + kNoAllocWords, (cudaStream_t)stream);
+  return run_plan_scratch(ctx, pl, in, out, cfg, scratch, scratch + kNoAllocWords, (cudaStream_t)stream);
 }

@@ -12,8 +12,12 @@
 // (a + b, (a - b) * w), one addmod, one submod, one mulmod: the butterfly of Sec. 5.3),
 // and writes the outputs back in contiguous runs.  DIF leaves each group's outputs in
 // bit-reversed position inside the tile; the store reads them through the bit reversal.
-// The last DIF stage has twiddle 1 and no multiplication; the first pass has Ns = 1 and
-// no pre-twiddles.
+// Twiddles equal to 1 are not multiplied: the whole last DIF stage, the first butterfly of
+// every block in the other stages, the k = 0 pre-twiddles and all of the first pass (Ns = 1).
+//
+// Values are kept lazily reduced inside a transform: every stage maps [0, 4q) to [0, 4q)
+// (the 4-bit headroom of a (W-4)-bit modulus keeps 8q below 2^W), and the last pass makes
+// its outputs canonical as it stores them.  Inputs must be canonical.
 //
 // Twiddles are in the reduction's domain: every table entry w carries its companion
 // floor(w * 2^(32L) / q), so a twiddle multiplication needs no double-width product
@@ -22,20 +26,16 @@
 
 #include "moma_internal.hpp"
 #include "moma_limbs.cuh"
+#include "moma_ntt_tile.cuh"
 
 namespace moma {
 
-constexpr int kNttThreads = 256;
+constexpr int kNttMaxThreads = 256;  // per CTA; the launch may use 32, 64, 128 or 256
 
-// Default CTA tile (elements) per width: the tile takes L*T*4 bytes of shared memory.
-int default_tile_log(int L) {
-  switch (L) {
-    case 4: return 12;   // 64 KiB
-    case 8: return 11;   // 64 KiB
-    case 12: return 11;  // 96 KiB
-    default: return 10;
-  }
-}
+// Default CTA tile (elements): 2^10 elements for 128 threads (L*4 KiB of shared memory);
+// measured best on GB300 for 128- to 384-bit transforms of 2^12 and 2^20 points.
+int default_tile_log(int L) { return L <= 12 ? 10 : 9; }
+constexpr int kDefaultThreads = 128;
 
 // Largest tile that fits the 227 KiB of shared memory one CTA may use.
 int max_tile_log(int L) {
@@ -44,15 +44,18 @@ int max_tile_log(int L) {
   return t;
 }
 
-constexpr int kDefaultEngine = 1;
+// Measured on GB300 (2^20-point transforms, 16 per call): whole-product rows are faster up to
+// 256 bits, carry chains at 384 bits.
+static int default_engine(int L) { return L <= 8 ? 2 : 1; }
 
 moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
-  moma_config c = {0, 0, 0, 0};
+  moma_config c = {0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(op, logn));
   if (it != ctx->configs.end()) c = it->second;
-  if (c.engine == 0) c.engine = kDefaultEngine;
+  if (c.engine == 0) c.engine = default_engine(ctx->L);
   if (c.tile_log == 0) c.tile_log = default_tile_log(ctx->L);
-  if (c.max_logr == 0) c.max_logr = c.tile_log > 6 ? c.tile_log - 5 : 1;
+  if (c.max_logr == 0) c.max_logr = c.tile_log > 6 ? c.tile_log - 5 : 1;  // >= 32 groups per tile
+  if (c.cta_threads == 0) c.cta_threads = kDefaultThreads;
   c.vec_width = 0;
   return c;
 }
@@ -62,143 +65,16 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
   if (c.engine < 0 || c.engine > 2) return false;
   if (c.tile_log != 0 && (c.tile_log < 5 || c.tile_log > max_tile_log(L))) return false;
   if (c.max_logr < 0 || (c.max_logr != 0 && c.tile_log != 0 && c.max_logr > c.tile_log)) return false;
+  if (c.cta_threads != 0 && c.cta_threads != 32 && c.cta_threads != 64 && c.cta_threads != 128 &&
+      c.cta_threads != 256)
+    return false;
   return true;
 }
 
-// XOR swizzle of a word index inside one limb plane of the tile: flips the low five
-// bits by the next five, so that both row-wise and bit-reversed column-wise accesses
-// spread over the 32 banks.  A bijection on every aligned block of 32 words.
-__device__ __forceinline__ uint32_t swz(uint32_t x) { return x ^ ((x >> 5) & 31u); }
-
-template <int L>
-struct NttPassArgs {
-  const uint32_t* src;
-  const uint32_t* src2;  // pointwise second operand (fused polynomial product), else null
-  uint32_t* dst;
-  const uint32_t* tw_pass;
-  const uint32_t* tw_int;
-  uint64_t tw_count;
-  uint64_t n;
-  uint32_t logR, logG, logNs;
-  uint32_t tiles_per_transform;
-  uint32_t flags;  // 1: pre-twiddle, 2: multiply by sc at load, 4: pointwise product at load
-  uint32_t sc[L], scp[L];
-  ModK<L> k;
-};
-
-enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4 };
-
 template <int L, bool WIDE>
-__global__ void __launch_bounds__(kNttThreads) ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
+__global__ void __launch_bounds__(kNttMaxThreads) ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ uint32_t sm[];
-  const uint32_t R = 1u << p.logR;
-  const uint32_t G = 1u << p.logG;
-  const uint32_t T = R << p.logG;
-  const uint32_t tile = blockIdx.x;
-  const uint64_t b = tile / p.tiles_per_transform;
-  const uint64_t jb = tile - b * p.tiles_per_transform;
-  const uint64_t base = b * (uint64_t)L * p.n;
-  const uint64_t j0 = jb << p.logG;
-  const uint64_t nR = p.n >> p.logR;
-  const uint64_t ns_mask = (1ull << p.logNs) - 1;
-
-  // ---- load (+ pointwise product, scaling, pre-twiddle) into the tile
-  for (uint32_t e = threadIdx.x; e < T; e += kNttThreads) {
-    const uint32_t r = e >> p.logG, g = e & (G - 1);
-    const uint64_t j = j0 + g;
-    const uint64_t idx = base + j + (uint64_t)r * nR;
-    uint32_t v[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) v[l] = p.src[idx + (uint64_t)l * p.n];
-    if (p.flags & F_POINTWISE) {
-      uint32_t u[L], t[L];
-#pragma unroll
-      for (int l = 0; l < L; ++l) u[l] = p.src2[idx + (uint64_t)l * p.n];
-      mulmod_barrett<L, WIDE>(t, v, u, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
-    }
-    if (p.flags & F_SCALE) {
-      uint32_t t[L];
-      mulmod_fixed<L, WIDE>(t, v, p.sc, p.scp, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
-    }
-    if ((p.flags & F_PRETW) && r != 0) {
-      const uint64_t ti = (uint64_t)(r - 1) * (ns_mask + 1) + (j & ns_mask);
-      uint32_t w[L], wp[L], t[L];
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        w[l] = __ldg(p.tw_pass + ti + (uint64_t)l * p.tw_count);
-        wp[l] = __ldg(p.tw_pass + ti + (uint64_t)(L + l) * p.tw_count);
-      }
-      mulmod_fixed<L, WIDE>(t, v, w, wp, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
-    }
-    const uint32_t a = swz(e);  // e = r*G + g
-#pragma unroll
-    for (int l = 0; l < L; ++l) sm[l * T + a] = v[l];
-  }
-  __syncthreads();
-
-  // ---- R-point transforms: logR radix-2 DIF stages, in place in the tile
-  const uint32_t half_int = R >> 1;
-#pragma unroll 1
-  for (uint32_t s = 0; s < p.logR; ++s) {
-    const uint32_t logh = p.logR - s - 1;
-    const uint32_t h = 1u << logh;
-    for (uint32_t bi = threadIdx.x; bi < (T >> 1); bi += kNttThreads) {
-      const uint32_t g = bi & (G - 1), u = bi >> p.logG;
-      const uint32_t i = u & (h - 1), blk = u >> logh;
-      const uint32_t p0 = (blk << (logh + 1)) + i;
-      const uint32_t a0 = swz((p0 << p.logG) + g), a1 = swz(((p0 + h) << p.logG) + g);
-      uint32_t x0[L], x1[L], y0[L], d[L];
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        x0[l] = sm[l * T + a0];
-        x1[l] = sm[l * T + a1];
-      }
-      addmod<L>(y0, x0, x1, p.k.q);
-      submod<L>(d, x0, x1, p.k.q);
-      if (logh != 0) {
-        const uint32_t ti = i << s;  // w_(2h)^i = w_R^(i * R/(2h))
-        uint32_t w[L], wp[L], y1[L];
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-          w[l] = __ldg(p.tw_int + ti + l * half_int);
-          wp[l] = __ldg(p.tw_int + ti + (L + l) * half_int);
-        }
-        mulmod_fixed<L, WIDE>(y1, d, w, wp, p.k);
-#pragma unroll
-        for (int l = 0; l < L; ++l) d[l] = y1[l];
-      }
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        sm[l * T + a0] = y0[l];
-        sm[l * T + a1] = d[l];
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- store: output s of group j goes to (j-k)*R + k + s*Ns; consecutive threads take
-  // consecutive addresses (k fastest, then s, then the Ns-blocks of the tile).
-  const uint32_t logGl = p.logG < p.logNs ? p.logG : p.logNs;
-  const uint32_t Gl = 1u << logGl;
-  for (uint32_t e = threadIdx.x; e < T; e += kNttThreads) {
-    const uint32_t gl = e & (Gl - 1);
-    const uint32_t sp = (e >> logGl) & (R - 1);
-    const uint32_t gh = e >> (logGl + p.logR);
-    const uint32_t g = (gh << logGl) + gl;
-    const uint64_t j = j0 + g;
-    const uint64_t kk = j & ns_mask;
-    const uint64_t addr = base + (j - kk) * R + kk + ((uint64_t)sp << p.logNs);
-    const uint32_t pr = __brev(sp) >> (32 - p.logR);
-    const uint32_t a = swz((pr << p.logG) + g);
-#pragma unroll
-    for (int l = 0; l < L; ++l) p.dst[addr + (uint64_t)l * p.n] = sm[l * T + a];
-  }
+  ntt_tile<L, WIDE>(p, blockIdx.x, sm);
 }
 
 // ------------------------------------------------------------------ twiddle tables
@@ -258,6 +134,7 @@ static void fill_modk(const moma_ctx* ctx, ModK<L>& k) {
     k.nq[i] = ctx->k.nq[i];
     k.mu[i] = ctx->k.mu[i];
     k.q2[i] = ctx->k.q2[i];
+    k.q4[i] = ctx->k.q4[i];
   }
 }
 
@@ -429,25 +306,9 @@ moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int ma
 
 template <int L, bool WIDE>
 static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
-                            const uint32_t* src2, uint32_t* dst, uint32_t flags, cudaStream_t st) {
+                            const uint32_t* src2, uint32_t* dst, uint32_t flags, int threads, cudaStream_t st) {
   NttPassArgs<L> a;
-  a.src = src;
-  a.src2 = src2;
-  a.dst = dst;
-  a.tw_pass = d.tw_pass;
-  a.tw_int = d.tw_int;
-  a.tw_count = d.tw_count;
-  a.n = 1ull << pl->logn;
-  a.logR = (uint32_t)d.logR;
-  a.logG = (uint32_t)d.logG;
-  a.logNs = (uint32_t)d.logNs;
-  a.tiles_per_transform = (uint32_t)(a.n >> (d.logR + d.logG));
-  a.flags = flags | (d.logNs > 0 ? F_PRETW : 0);
-  for (int i = 0; i < L; ++i) {
-    a.sc[i] = pl->scale[i];
-    a.scp[i] = pl->scalep[i];
-  }
-  fill_modk<L>(ctx, a.k);
+  fill_pass_args<L>(ctx, pl, d, count, src, src2, dst, flags, a);
   const size_t smem = (size_t)L * 4u << (d.logR + d.logG);
   static bool attr_done = false;
   if (!attr_done) {
@@ -459,20 +320,22 @@ static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, si
   const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
   if (grid == 0) return MOMA_OK;
   if (grid > 0x7fffffffull) return MOMA_ERR_SIZE;
-  ntt_pass_kernel<L, WIDE><<<(unsigned)grid, kNttThreads, smem, st>>>(a);
+  ntt_pass_kernel<L, WIDE><<<(unsigned)grid, threads, smem, st>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
 static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
-                              const uint32_t* src2, uint32_t* dst, uint32_t flags, int engine, cudaStream_t st) {
-  const bool wide = engine == 2;
+                              const uint32_t* src2, uint32_t* dst, uint32_t flags, const moma_config& cfg,
+                              cudaStream_t st) {
+  const bool wide = cfg.engine == 2;
+  const int th = cfg.cta_threads;
   switch (ctx->L) {
-    case 4: return wide ? run_pass<4, true>(ctx, pl, d, count, src, src2, dst, flags, st)
-                        : run_pass<4, false>(ctx, pl, d, count, src, src2, dst, flags, st);
-    case 8: return wide ? run_pass<8, true>(ctx, pl, d, count, src, src2, dst, flags, st)
-                        : run_pass<8, false>(ctx, pl, d, count, src, src2, dst, flags, st);
-    case 12: return wide ? run_pass<12, true>(ctx, pl, d, count, src, src2, dst, flags, st)
-                         : run_pass<12, false>(ctx, pl, d, count, src, src2, dst, flags, st);
+    case 4: return wide ? run_pass<4, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                        : run_pass<4, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    case 8: return wide ? run_pass<8, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                        : run_pass<8, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    case 12: return wide ? run_pass<12, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                         : run_pass<12, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   }
   return MOMA_ERR_UNSUPPORTED;
 }
@@ -480,7 +343,7 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
 // Run every pass of a plan: in -> [scratch1 -> scratch2 -> ...] -> out.  The first pass can
 // fuse a pointwise product with src2 (polymul) and, for the inverse, the n^-1 scaling.
 static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
-                            uint32_t* out, int engine, cudaStream_t st) {
+                            uint32_t* out, const moma_config& cfg, cudaStream_t st) {
   const size_t P = pl->passes.size();
   const size_t words = (size_t)ctx->L * ((size_t)1 << pl->logn) * count;
   uint32_t* s1 = nullptr;
@@ -494,10 +357,10 @@ static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const u
   const uint32_t* src = in;
   for (size_t i = 0; i < P && rc == MOMA_OK; ++i) {
     uint32_t* dst = (i + 1 == P) ? out : ((i % 2 == 0) ? s1 : s2);
-    uint32_t flags = 0;
+    uint32_t flags = (i + 1 == P) ? F_LAST : 0;
     if (i == 0 && in2) flags |= F_POINTWISE;
     if (i == 0 && pl->inverse) flags |= F_SCALE;
-    rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, engine, st);
+    rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, cfg, st);
     src = dst;
   }
   if (s1) cudaFreeAsync(s1, st);
@@ -512,15 +375,15 @@ Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_log
   return it == ctx->plans.end() ? nullptr : it->second;
 }
 
-moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out, int engine,
-                             uint32_t* s1, uint32_t* s2, cudaStream_t st) {
+moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out,
+                             const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st) {
   const size_t P = pl->passes.size();
   moma_status rc = MOMA_OK;
   const uint32_t* src = in;
   for (size_t i = 0; i < P && rc == MOMA_OK; ++i) {
     uint32_t* dst = (i + 1 == P) ? out : ((i % 2 == 0) ? s1 : s2);
-    const uint32_t flags = (i == 0 && pl->inverse) ? F_SCALE : 0;
-    rc = run_pass_l(ctx, pl, pl->passes[i], 1, src, nullptr, dst, flags, engine, st);
+    const uint32_t flags = ((i == 0 && pl->inverse) ? F_SCALE : 0) | ((i + 1 == P) ? F_LAST : 0);
+    rc = run_pass_l(ctx, pl, pl->passes[i], 1, src, nullptr, dst, flags, cfg, st);
     src = dst;
   }
   return rc;
@@ -532,7 +395,7 @@ moma_status launch_ntt_cfg(moma_ctx* ctx, int logn, size_t count, bool inverse, 
   moma_status rc = get_plan(ctx, logn, inverse, cfg.tile_log, cfg.max_logr, &pl);
   if (rc) return rc;
   if (count == 0) return MOMA_OK;
-  return run_plan(ctx, pl, count, in, nullptr, out, cfg.engine, st);
+  return run_plan(ctx, pl, count, in, nullptr, out, cfg, st);
 }
 
 moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in, uint32_t* out,
@@ -552,9 +415,9 @@ moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const
   uint32_t* fa = nullptr;
   if (cudaMallocAsync(&fa, 2 * words * 4, st) != cudaSuccess) return MOMA_ERR_OOM;
   uint32_t* fb = fa + words;
-  rc = run_plan(ctx, fw, 1, a, nullptr, fa, cfg.engine, st);
-  if (!rc) rc = run_plan(ctx, fw, 1, b, nullptr, fb, cfg.engine, st);
-  if (!rc) rc = run_plan(ctx, iv, 1, fa, fb, c, cfg.engine, st);
+  rc = run_plan(ctx, fw, 1, a, nullptr, fa, cfg, st);
+  if (!rc) rc = run_plan(ctx, fw, 1, b, nullptr, fb, cfg, st);
+  if (!rc) rc = run_plan(ctx, iv, 1, fa, fb, c, cfg, st);
   cudaFreeAsync(fa, st);
   return rc;
 }

@@ -1,0 +1,200 @@
+// moma_ntt_tile.cuh -- one CTA tile of a Stockham NTT pass (device code shared by the
+// per-pass kernels of moma_ntt.cu and the persistent batch kernel of moma_batch.cu).
+#pragma once
+#include "moma_internal.hpp"
+#include "moma_limbs.cuh"
+
+namespace moma {
+
+// XOR swizzle of a word index inside one limb plane of the tile: flips the low five
+// bits by the next five, so that both row-wise and bit-reversed column-wise accesses
+// spread over the 32 banks.  A bijection on every aligned block of 32 words.
+__device__ __forceinline__ uint32_t swz(uint32_t x) { return x ^ ((x >> 5) & 31u); }
+
+template <int L>
+struct NttPassArgs {
+  const uint32_t* src;
+  const uint32_t* src2;  // pointwise second operand (fused polynomial product), else null
+  uint32_t* dst;
+  const uint32_t* tw_pass;
+  const uint32_t* tw_int;
+  uint64_t tw_count;
+  uint64_t n;
+  uint32_t logR, logG, logNs;
+  uint32_t tiles_per_transform;
+  uint32_t flags;  // F_* below
+  uint32_t sc[L], scp[L];
+  ModK<L> k;
+};
+
+// F_PRETW: pre-twiddles (Ns > 1); F_SCALE: multiply by sc at load (n^-1 of the inverse);
+// F_POINTWISE: product with src2 at load (fused polynomial product); F_LAST: canonical store.
+enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4, F_LAST = 8 };
+
+// DIF butterfly on lazy values: a, b in [0, 4q) -> (a + b, (a - b) * w) both in [0, 4q).
+// With MUL false the twiddle is 1.
+template <int L, bool WIDE>
+__device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&b)[L], bool mul,
+                                                   const uint32_t* twp, uint32_t tw_stride, const ModK<L>& k) {
+  uint32_t x[L], d[L];
+  add_words<L, false>(x, a, b);  // [0, 8q)
+  cond_sub<L>(x, k.q4);           // [0, 4q)
+  add_words<L, false>(d, a, k.q4);
+  sub_words<L, false>(d, d, b);   // a + 4q - b in (0, 8q)
+  if (mul) {
+    uint32_t w[L], wp[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      w[l] = __ldg(twp + l * tw_stride);
+      wp[l] = __ldg(twp + (L + l) * tw_stride);
+    }
+    mulmod_fixed_lazy<L, WIDE>(b, d, w, wp, k);  // [0, 3q)
+  } else {
+    cond_sub<L>(d, k.q4);
+#pragma unroll
+    for (int l = 0; l < L; ++l) b[l] = d[l];
+  }
+#pragma unroll
+  for (int l = 0; l < L; ++l) a[l] = x[l];
+}
+
+// One CTA tile of one Stockham pass: `tile` indexes (transform, group block).  `sm` holds
+// L*R*G words.  Used by the per-pass kernel and by the persistent batch kernel; source data
+// are read with L2-only loads so that data written earlier in the same persistent launch by
+// other SMs is never served from a stale L1 line.
+template <int L, bool WIDE>
+__device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm) {
+  const uint32_t R = 1u << p.logR;
+  const uint32_t G = 1u << p.logG;
+  const uint32_t T = R << p.logG;
+  const uint64_t b = tile / p.tiles_per_transform;
+  const uint64_t jb = tile - b * p.tiles_per_transform;
+  const uint64_t base = b * (uint64_t)L * p.n;
+  const uint64_t j0 = jb << p.logG;
+  const uint64_t nR = p.n >> p.logR;
+  const uint64_t ns_mask = (1ull << p.logNs) - 1;
+
+  // ---- load (+ pointwise product, scaling, pre-twiddle) into the tile
+  for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+    const uint32_t r = e >> p.logG, g = e & (G - 1);
+    const uint64_t j = j0 + g;
+    const uint64_t idx = base + j + (uint64_t)r * nR;
+    uint32_t v[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = __ldcg(p.src + idx + (uint64_t)l * p.n);
+    if (p.flags & F_POINTWISE) {
+      uint32_t u[L], t[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) u[l] = __ldcg(p.src2 + idx + (uint64_t)l * p.n);
+      mulmod_barrett<L, WIDE>(t, v, u, p.k);
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l] = t[l];
+    }
+    if (p.flags & F_SCALE) {
+      uint32_t t[L];
+      mulmod_fixed_lazy<L, WIDE>(t, v, p.sc, p.scp, p.k);
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l] = t[l];
+    }
+    if ((p.flags & F_PRETW) && r != 0 && (j & ns_mask) != 0) {
+      const uint64_t ti = (uint64_t)(r - 1) * (ns_mask + 1) + (j & ns_mask);
+      uint32_t w[L], wp[L], t[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        w[l] = __ldg(p.tw_pass + ti + (uint64_t)l * p.tw_count);
+        wp[l] = __ldg(p.tw_pass + ti + (uint64_t)(L + l) * p.tw_count);
+      }
+      mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l] = t[l];
+    }
+    const uint32_t a = swz(e);  // e = r*G + g
+#pragma unroll
+    for (int l = 0; l < L; ++l) sm[l * T + a] = v[l];
+  }
+  __syncthreads();
+
+  // ---- R-point transforms: logR radix-2 DIF stages, in place in the tile
+  const uint32_t half_int = R >> 1;
+#pragma unroll 1
+  for (uint32_t s = 0; s < p.logR; ++s) {
+    const uint32_t logh = p.logR - s - 1;
+    const uint32_t h = 1u << logh;
+    for (uint32_t bi = threadIdx.x; bi < (T >> 1); bi += blockDim.x) {
+      const uint32_t g = bi & (G - 1), u = bi >> p.logG;
+      const uint32_t i = u & (h - 1), blk = u >> logh;
+      const uint32_t p0 = (blk << (logh + 1)) + i;
+      const uint32_t a0 = swz((p0 << p.logG) + g), a1 = swz(((p0 + h) << p.logG) + g);
+      uint32_t x0[L], x1[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        x0[l] = sm[l * T + a0];
+        x1[l] = sm[l * T + a1];
+      }
+      // twiddle w_(2h)^i = w_R^(i * R/(2h)); 1 for i = 0 and in the last stage (h = 1)
+      dif_butterfly_lazy<L, WIDE>(x0, x1, i != 0, p.tw_int + (i << s), half_int, p.k);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        sm[l * T + a0] = x0[l];
+        sm[l * T + a1] = x1[l];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- store: output s of group j goes to (j-k)*R + k + s*Ns; consecutive threads take
+  // consecutive addresses (k fastest, then s, then the Ns-blocks of the tile).
+  const uint32_t logGl = p.logG < p.logNs ? p.logG : p.logNs;
+  const uint32_t Gl = 1u << logGl;
+  for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
+    const uint32_t gl = e & (Gl - 1);
+    const uint32_t sp = (e >> logGl) & (R - 1);
+    const uint32_t gh = e >> (logGl + p.logR);
+    const uint32_t g = (gh << logGl) + gl;
+    const uint64_t j = j0 + g;
+    const uint64_t kk = j & ns_mask;
+    const uint64_t addr = base + (j - kk) * R + kk + ((uint64_t)sp << p.logNs);
+    const uint32_t pr = __brev(sp) >> (32 - p.logR);
+    const uint32_t a = swz((pr << p.logG) + g);
+    uint32_t v[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = sm[l * T + a];
+    if (p.flags & F_LAST) {  // [0, 4q) -> [0, q)
+      cond_sub<L>(v, p.k.q2);
+      cond_sub<L>(v, p.k.q);
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) p.dst[addr + (uint64_t)l * p.n] = v[l];
+  }
+}
+
+// Host: fill the arguments of one pass (count transforms of length 2^logn).
+template <int L>
+inline void fill_pass_args(const moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count,
+                           const uint32_t* src, const uint32_t* src2, uint32_t* dst, uint32_t flags,
+                           NttPassArgs<L>& a) {
+  a.src = src;
+  a.src2 = src2;
+  a.dst = dst;
+  a.tw_pass = d.tw_pass;
+  a.tw_int = d.tw_int;
+  a.tw_count = d.tw_count;
+  a.n = 1ull << pl->logn;
+  a.logR = (uint32_t)d.logR;
+  a.logG = (uint32_t)d.logG;
+  a.logNs = (uint32_t)d.logNs;
+  a.tiles_per_transform = (uint32_t)(a.n >> (d.logR + d.logG));
+  a.flags = flags | (d.logNs > 0 ? F_PRETW : 0);
+  for (int i = 0; i < L; ++i) {
+    a.sc[i] = pl->scale[i];
+    a.scp[i] = pl->scalep[i];
+    a.k.q[i] = ctx->k.q[i];
+    a.k.nq[i] = ctx->k.nq[i];
+    a.k.mu[i] = ctx->k.mu[i];
+    a.k.q2[i] = ctx->k.q2[i];
+    a.k.q4[i] = ctx->k.q4[i];
+  }
+  (void)count;
+}
+
+}  // namespace moma

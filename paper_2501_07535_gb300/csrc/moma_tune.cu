@@ -90,22 +90,25 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
     if (count == 0) count = 1;
     if (op == MOMA_OP_POLYMUL) count = 1;
-    const int t0 = default_tile_log(ctx->L);
+    // CTA size and tile go together: 2^3..2^4 elements per thread; radices leave 8 to 32
+    // groups per tile.
     for (int engine = 1; engine <= 2; ++engine)
-      for (int t = t0 - 1; t <= t0 + 1; ++t) {
-        if (t < 5 || t > max_tile_log(ctx->L)) continue;
-        if (lg <= t) {
-          cands.push_back({engine, t, t, 0});
-          continue;
+      for (int th = 32, lth = 5; th <= 256; th *= 2, ++lth)
+        for (int t = 0; t <= 1; ++t) {
+          const int tl = lth + 3 + t;
+          if (tl > max_tile_log(ctx->L)) continue;
+          if (lg <= tl) {
+            cands.push_back({engine, tl, tl, 0, th});
+            continue;
+          }
+          for (int r = tl - 3; r >= tl - 5; --r)
+            if (r >= 1) cands.push_back({engine, tl, r, 0, th});
         }
-        for (int r = t - 3; r >= t - 5; --r)
-          if (r >= 1) cands.push_back({engine, t, r, 0});
-      }
   } else if (is_vec_op(op)) {
     if (n == 0) return MOMA_ERR_SIZE;
     const bool mul = op == MOMA_OP_MUL || op == MOMA_OP_AXPY;
     for (int engine = 1; engine <= (mul ? 2 : 1); ++engine)
-      for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v});
+      for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v, 0});
   } else {
     return MOMA_ERR_INVALID_ARG;
   }
@@ -130,7 +133,7 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MOMA_ERR_CUDA;
   double best_t = 1e30;
-  moma_config best_c = cands.empty() ? moma_config{0, 0, 0, 0} : cands[0];
+  moma_config best_c = cands.empty() ? moma_config{0, 0, 0, 0, 0} : cands[0];
   moma_status rc = MOMA_OK;
   for (const auto& cfg : cands) {
     rc = run(cfg);  // first use builds the plan (twiddle tables) outside the timing

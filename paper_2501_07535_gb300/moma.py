@@ -59,14 +59,25 @@ _SIGS = {
     "moma_ctx_get_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
     "moma_autotune": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _SZ, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "moma_ntt_fwd_noalloc": (ctypes.c_int, [_P, _SZ, _P, _P, _P]),
+    "moma_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "moma_batch_run": (ctypes.c_int, [_P, _P]),
+    "moma_batch_sync_status": (ctypes.c_int, [_P]),
+    "moma_batch_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "moma_batch_inject_missing_dependency": (ctypes.c_int, [_P]),
+    "moma_batch_destroy": (None, [_P]),
+    "moma_batch_submit": (ctypes.c_int, [_P, ctypes.c_int, _P]),
 }
 
 OPS = {"ntt_fwd": 0, "ntt_inv": 1, "polymul": 2, "add": 3, "sub": 4, "mul": 5, "axpy": 6}
 
 
+class moma_job(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("ctx", _P), ("n", _SZ), ("a", _P), ("b", _P), ("out", _P), ("alpha", _P)]
+
+
 class moma_config(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("tile_log", ctypes.c_int), ("max_logr", ctypes.c_int),
-                ("vec_width", ctypes.c_int)]
+                ("vec_width", ctypes.c_int), ("cta_threads", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -213,8 +224,8 @@ def _op(op) -> int:
     return OPS[op] if isinstance(op, str) else int(op)
 
 
-def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0):
-    cfg = moma_config(engine, tile_log, max_logr, vec_width)
+def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0, cta_threads=0):
+    cfg = moma_config(engine, tile_log, max_logr, vec_width, cta_threads)
     _check(lib().moma_ctx_set_config(ctx, _op(op), n, ctypes.byref(cfg)), "moma_ctx_set_config")
 
 
@@ -231,6 +242,56 @@ def moma_autotune(ctx, op, n, count=1, stream=None):
     _check(lib().moma_autotune(ctx, _op(op), n, count, _stream_handle(stream), ctypes.byref(cfg),
                                ctypes.byref(us)), "moma_autotune")
     return cfg.as_dict(), us.value
+
+
+def _jobs_array(jobs):
+    """jobs: list of dicts {op, ctx, n, a, b, out, alpha}; tensors or raw pointers."""
+    arr = (moma_job * len(jobs))()
+    keep = []
+    for i, j in enumerate(jobs):
+        def p(x):
+            if x is None:
+                return None
+            return x if isinstance(x, int) else _ptr(x)
+        alpha = None
+        if j.get("alpha") is not None:
+            al = _limbs_array(j["alpha"], moma_ctx_limbs(j["ctx"]))
+            keep.append(al)
+            alpha = ctypes.cast(al, _P)
+        arr[i] = moma_job(_op(j["op"]), j["ctx"], j["n"], p(j["a"]), p(j.get("b")), p(j["out"]), alpha)
+    return arr, keep
+
+
+def moma_batch_create(jobs) -> int:
+    arr, keep = _jobs_array(jobs)
+    h = _P()
+    _check(lib().moma_batch_create(ctypes.cast(arr, _P), len(jobs), ctypes.byref(h)), "moma_batch_create")
+    return h.value
+
+
+def moma_batch_run(batch, stream=None):
+    _check(lib().moma_batch_run(batch, _stream_handle(stream)), "moma_batch_run")
+
+
+def moma_batch_sync_status(batch) -> int:
+    return lib().moma_batch_sync_status(batch)
+
+
+def moma_batch_set_wait_limit(batch, polls: int):
+    _check(lib().moma_batch_set_wait_limit(batch, polls), "moma_batch_set_wait_limit")
+
+
+def moma_batch_inject_missing_dependency(batch):
+    _check(lib().moma_batch_inject_missing_dependency(batch), "moma_batch_inject_missing_dependency")
+
+
+def moma_batch_destroy(batch):
+    lib().moma_batch_destroy(batch)
+
+
+def moma_batch_submit(jobs, stream=None) -> int:
+    arr, keep = _jobs_array(jobs)
+    return lib().moma_batch_submit(ctypes.cast(arr, _P), len(jobs), _stream_handle(stream))
 
 
 # ----------------------------------------------------------------- conveniences

@@ -18,14 +18,15 @@ def test_ntt_every_engine_and_split(gpu, width, engine):
     p = inputs.prime(width)
     ctx = gpu.moma_ctx_create(p.q, width)
     try:
-        for lg, tile, rmax in ((10, 11, 6), (13, 10, 5), (13, 11, 8), (15, 12, 7)):
+        for lg, tile, rmax, th in ((10, 11, 6, 256), (13, 10, 5, 256), (13, 11, 8, 128), (15, 12, 7, 256),
+                                   (13, 8, 5, 32), (16, 9, 6, 64), (10, 10, 7, 128), (7, 8, 5, 32)):
             if tile > 12 and p.L == 12:
                 continue
             n = 1 << lg
-            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, engine=engine, tile_log=tile, max_logr=rmax)
-            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, engine=engine, tile_log=tile, max_logr=rmax)
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, engine=engine, tile_log=tile, max_logr=rmax, cta_threads=th)
+            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, engine=engine, tile_log=tile, max_logr=rmax, cta_threads=th)
             cfg = gpu.moma_ctx_get_config(ctx, "ntt_fwd", n)
-            assert (cfg["engine"], cfg["tile_log"], cfg["max_logr"]) == (engine, tile, rmax)
+            assert (cfg["engine"], cfg["tile_log"], cfg["max_logr"], cfg["cta_threads"]) == (engine, tile, rmax, th)
             x = inputs.residues(p.q, p.L, n, seed=lg + engine)
             dx = gpu.to_device(x)
             dy = torch.empty_like(dx)
