@@ -179,9 +179,10 @@ typedef struct moma_batch moma_batch;
  * are fixed at creation; refill the same input buffers between runs.  Synchronous. */
 moma_status moma_batch_create(const moma_job *jobs, int njobs, moma_batch **out);
 
-/* Run the batch on `stream` (asynchronous).  On a non-default stream the first run
- * captures the launch sequence in a CUDA graph and later runs replay it; on the legacy
- * default stream, or while the caller is capturing, it launches directly. */
+/* Run the batch on `stream` (asynchronous).  The first run launches directly; on a
+ * non-default stream the second run captures the launch sequence in a CUDA graph and later
+ * runs replay it.  On the legacy default stream, or while the caller is capturing, every run
+ * launches directly. */
 moma_status moma_batch_run(moma_batch *batch, void *stream);
 
 /* Wait for the device, then return and clear the batch's device-side status:
@@ -197,6 +198,9 @@ moma_status moma_batch_set_wait_limit(moma_batch *batch, uint64_t polls);
  * to exercise the bounded wait (the next run reports MOMA_ERR_TIMEOUT). */
 moma_status moma_batch_inject_missing_dependency(moma_batch *batch);
 
+/* Release the batch.  Its device memory is returned stream-ordered on an internal stream, so
+ * the call does not wait for the device; the caller must make sure no run of the batch is
+ * still executing (e.g. synchronise its stream or an event recorded after the last run). */
 void moma_batch_destroy(moma_batch *batch);
 
 /* create + run on `stream` + wait + destroy; returns the device-side status. */

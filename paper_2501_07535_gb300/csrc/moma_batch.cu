@@ -18,6 +18,7 @@
 // width on GB300); results are identical either way.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -156,6 +157,7 @@ using namespace moma;
 
 struct moma_batch {
   int device = 0;
+  int runs = 0;
   std::vector<Seg> segs;
   uint32_t total = 0;
   uint32_t ncounters = 0;
@@ -172,6 +174,18 @@ struct moma_batch {
 };
 
 namespace {
+
+// Per-device stream for batch set-up and tear-down: allocations and uploads are stream-ordered
+// there (cudaMallocAsync / cudaFreeAsync), so creating or destroying a batch never waits for
+// the work other streams have in flight.
+cudaStream_t setup_stream(int dev) {
+  static std::mutex lock;
+  static cudaStream_t streams[64] = {};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(lock);
+  if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+  return streams[dev];
+}
 
 struct ArgBuf {
   std::vector<uint8_t> bytes;
@@ -339,7 +353,12 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
   moma_batch* b = new (std::nothrow) moma_batch();
   if (!b) return MOMA_ERR_OOM;
   b->device = dev;
-  if (scratch_words && cudaMalloc(&b->d_scratch, scratch_words * 4) != cudaSuccess) {
+  cudaStream_t ss = setup_stream(dev);
+  if (!ss) {
+    delete b;
+    return MOMA_ERR_CUDA;
+  }
+  if (scratch_words && cudaMallocAsync(&b->d_scratch, scratch_words * 4, ss) != cudaSuccess) {
     delete b;
     return MOMA_ERR_OOM;
   }
@@ -400,10 +419,10 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
   std::stable_sort(pend.begin(), pend.end(), [](const PendingSeg& x, const PendingSeg& y) {
     return std::make_tuple(x.level, x.job, x.sub) < std::make_tuple(y.level, y.job, y.sub);
   });
-  if (cudaMalloc(&b->d_args, std::max<size_t>(ab.bytes.size(), 16)) != cudaSuccess ||
-      cudaMalloc(&b->d_segs, pend.size() * sizeof(Seg)) != cudaSuccess ||
-      cudaMalloc(&b->d_ctr, (1 + counter) * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+  if (cudaMallocAsync(&b->d_args, std::max<size_t>(ab.bytes.size(), 16), ss) != cudaSuccess ||
+      cudaMallocAsync(&b->d_segs, pend.size() * sizeof(Seg), ss) != cudaSuccess ||
+      cudaMallocAsync(&b->d_ctr, (1 + counter) * sizeof(uint32_t), ss) != cudaSuccess ||
+      cudaMallocAsync(&b->d_status, sizeof(int), ss) != cudaSuccess) {
     moma_batch_destroy(b);
     return MOMA_ERR_OOM;
   }
@@ -420,9 +439,10 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
   }
   b->total = (uint32_t)total;
   b->ncounters = counter;
-  if (cudaMemcpy(b->d_args, ab.bytes.data(), ab.bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
+  if (cudaMemcpyAsync(b->d_args, ab.bytes.data(), ab.bytes.size(), cudaMemcpyHostToDevice, ss) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ss) !=
+          cudaSuccess ||
+      cudaMemsetAsync(b->d_status, 0, sizeof(int), ss) != cudaSuccess || cudaStreamSynchronize(ss) != cudaSuccess) {
     moma_batch_destroy(b);
     return MOMA_ERR_CUDA;
   }
@@ -468,8 +488,9 @@ extern "C" moma_status moma_batch_run(moma_batch* b, void* stream) {
     }
   }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (st == nullptr || cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
-    return batch_launch(b, st);  // legacy stream, or already inside the caller's capture
+  if (st == nullptr || b->runs++ == 0 || cudaStreamIsCapturing(st, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone)
+    return batch_launch(b, st);  // legacy stream, first run, or inside the caller's capture
   if (!b->graph) {
     // capture the counter reset and the persistent launch once, replay it afterwards
     cudaGraph_t g = nullptr;
@@ -519,11 +540,9 @@ extern "C" moma_status moma_batch_inject_missing_dependency(moma_batch* b) {
 extern "C" void moma_batch_destroy(moma_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  if (b->d_segs) cudaFree(b->d_segs);
-  if (b->d_args) cudaFree(b->d_args);
-  if (b->d_ctr) cudaFree(b->d_ctr);
-  if (b->d_status) cudaFree(b->d_status);
-  if (b->d_scratch) cudaFree(b->d_scratch);
+  cudaStream_t ss = setup_stream(b->device);
+  for (void* p : {(void*)b->d_segs, (void*)b->d_args, (void*)b->d_ctr, (void*)b->d_status, (void*)b->d_scratch})
+    if (p) cudaFreeAsync(p, ss);
   delete b;
 }
 

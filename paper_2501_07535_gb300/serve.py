@@ -1,0 +1,260 @@
+"""Serving: continuous batching of arriving transform and BLAS jobs on one GPU.
+
+Requests arrive over time (a seeded Poisson stream).  The scheduler keeps a FIFO of
+arrived jobs and, whenever a slot is free, admits jobs from the head of the queue as long as
+their device memory (operands, output, transform scratch) fits the HBM budget, and launches
+them together as one persistent batch on one of several streams.  Micro-batches admitted while
+others are still on the GPU run concurrently with them; a finished batch frees its slot and its
+budget, and the next admission round takes the jobs that arrived meanwhile.  Twiddle tables and
+operands stay resident on the device across jobs (one context per modulus; inputs come from a
+per-(modulus, size) device cache).  Latency of a job = its batch's device completion time
+minus its arrival time.
+
+`Scheduler` is the host logic only (no CUDA), driven by an executor with launch/poll/footprint;
+`GpuExecutor` is the CUDA one.  `serve()` runs a stream and returns throughput and latency
+percentiles.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs
+
+BUDGET_BYTES = 40 * 10**9  # device memory admission budget
+
+
+@dataclass
+class _Inflight:
+    handle: object
+    jobs: list
+    nbytes: int
+
+
+@dataclass
+class ServeStats:
+    n_jobs: int
+    completed: int
+    rejected: int
+    makespan_s: float
+    latencies_s: list = field(repr=False)
+    batches: int = 0
+    max_inflight_bytes: int = 0
+    max_concurrent_batches: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_s) if self.latencies_s else np.zeros(1)
+        return {"jobs": self.n_jobs, "completed": self.completed, "rejected": self.rejected,
+                "makespan_s": round(self.makespan_s, 4),
+                "jobs_per_s": round(self.completed / self.makespan_s, 1) if self.makespan_s > 0 else None,
+                "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                "mean_ms": round(float(lat.mean()) * 1e3, 3), "batches": self.batches,
+                "max_concurrent_batches": self.max_concurrent_batches,
+                "max_inflight_gb": round(self.max_inflight_bytes / 1e9, 3)}
+
+
+class Scheduler:
+    """Admission by memory budget, a fixed number of concurrent micro-batches, FIFO order."""
+
+    def __init__(self, executor, budget_bytes: int = BUDGET_BYTES, slots: int = 4, max_batch_jobs: int = 64,
+                 clock=time.perf_counter, idle_sleep_s: float = 20e-6):
+        self.ex = executor
+        self.budget = budget_bytes
+        self.slots = slots
+        self.max_batch = max_batch_jobs
+        self.clock = clock
+        self.idle_sleep = idle_sleep_s
+
+    def run(self, arrivals, jobs) -> ServeStats:
+        n = len(jobs)
+        order = sorted(range(n), key=lambda i: arrivals[i])
+        queue = deque()
+        inflight: list[_Inflight] = []
+        done = [None] * n
+        rejected = []
+        used = 0
+        stats = ServeStats(n_jobs=n, completed=0, rejected=0, makespan_s=0.0, latencies_s=[])
+        t0 = self.clock()
+        self.ex.start(t0)
+        nxt = 0
+        while nxt < n or queue or inflight:
+            now = self.clock() - t0
+            while nxt < n and arrivals[order[nxt]] <= now:
+                queue.append(order[nxt])
+                nxt += 1
+            progressed = False
+            keep = []
+            for f in inflight:
+                t_done = self.ex.poll(f.handle)
+                if t_done is None:
+                    keep.append(f)
+                    continue
+                for j in f.jobs:
+                    done[j] = t_done
+                used -= f.nbytes
+                progressed = True
+            inflight = keep
+            while queue and len(inflight) < self.slots:
+                batch, nbytes = [], 0
+                while queue and len(batch) < self.max_batch:
+                    j = queue[0]
+                    need = self.ex.footprint(jobs[j])
+                    if need > self.budget:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+                        rejected.append(j)
+                        queue.popleft()
+                        continue
+                    if used + nbytes + need > self.budget:
+                        break
+                    batch.append(j)
+                    nbytes += need
+                    queue.popleft()
+                if not batch:
+                    break
+                handle = self.ex.launch([jobs[j] for j in batch])
+                inflight.append(_Inflight(handle, batch, nbytes))
+                used += nbytes
+                stats.batches += 1
+                stats.max_inflight_bytes = max(stats.max_inflight_bytes, used)
+                stats.max_concurrent_batches = max(stats.max_concurrent_batches, len(inflight))
+                progressed = True
+            if not progressed:
+                if not inflight and not queue and nxt < n:
+                    wait = arrivals[order[nxt]] - (self.clock() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                else:
+                    time.sleep(self.idle_sleep)
+        finished = [j for j in range(n) if done[j] is not None]
+        stats.completed = len(finished)
+        stats.rejected = len(rejected)
+        stats.latencies_s = [done[j] - arrivals[j] for j in finished]
+        stats.makespan_s = max((done[j] for j in finished), default=0.0) - min(arrivals, default=0.0)
+        self.rejected = rejected
+        return stats
+
+
+class GpuExecutor:
+    """Runs each micro-batch as one persistent batch launch on the next free stream."""
+
+    def __init__(self, contexts, slots: int = 4, keep_outputs: bool = False, master_log: int = 20):
+        import torch
+
+        from . import moma
+        self.torch, self.moma = torch, moma
+        self.ctx = contexts
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.free_streams = list(range(slots))
+        self.keep = keep_outputs
+        self.master_log = master_log
+        self._masters = {}
+        self._inputs = {}
+        self.outputs = {}
+
+    # -- device-resident operands: one seeded master per (modulus, operand); larger inputs
+    #    repeat it, smaller ones are a prefix of each limb plane (still uniform residues)
+    def _master(self, width, prime_seed, which):
+        key = (width, prime_seed, which)
+        if key not in self._masters:
+            p = inputs.prime(width, prime_seed)
+            self._masters[key] = self.moma.to_device(
+                inputs.residues(p.q, p.L, 1 << self.master_log, 900 + 10 * prime_seed + which + width))
+        return self._masters[key]
+
+    def operand(self, job, which):
+        key = (job.width, job.prime_seed, job.n, which)
+        t = self._inputs.get(key)
+        if t is None:
+            m = self._master(job.width, job.prime_seed, which)
+            N = m.shape[1]
+            if job.n <= N:
+                t = m[:, :job.n].contiguous()
+            else:
+                t = m.repeat(1, job.n // N).contiguous()
+            self._inputs[key] = t
+        return t
+
+    def footprint(self, job) -> int:
+        L = job.width // 32
+        vec = 4 * L * job.n
+        if job.op in ("ntt_fwd", "ntt_inv"):
+            return vec * 4  # input, output, two scratch buffers
+        if job.op == "polymul":
+            return vec * 9
+        return vec * 3
+
+    def prewarm(self, jobs):
+        """Build every transform plan (twiddle tables) and operand the stream will use."""
+        seen = set()
+        for j in jobs:
+            self.operand(j, 0)
+            if j.op not in ("ntt_fwd", "ntt_inv"):
+                self.operand(j, 1)
+            key = (j.width, j.prime_seed, j.n, j.op)
+            if j.op in ("ntt_fwd", "ntt_inv", "polymul") and key not in seen:
+                seen.add(key)
+                x = self.operand(j, 0)
+                out = self.torch.empty_like(x)
+                c = self.ctx.get(j.width, j.prime_seed)
+                (self.moma.moma_ntt_fwd if j.op == "ntt_fwd" else self.moma.moma_ntt_inv)(c, j.n, x, out)
+        self.torch.cuda.synchronize()
+
+    def start(self, t0):
+        self.base = self.torch.cuda.Event(enable_timing=True)
+        self.base.record()
+        self.base.synchronize()
+        self.t0 = t0
+        self.t_base = time.perf_counter() - t0  # host time of the base event, relative to t0
+
+    def launch(self, jobs):
+        torch, moma = self.torch, self.moma
+        sid = self.free_streams.pop(0)
+        st = self.streams[sid]
+        dicts, outs = [], []
+        for j in jobs:
+            a = self.operand(j, 0)
+            b = self.operand(j, 1) if j.op not in ("ntt_fwd", "ntt_inv") else None
+            with torch.cuda.stream(st):
+                out = torch.empty_like(a)
+            outs.append(out)
+            alpha = inputs.scalar_residue(inputs.prime(j.width, j.prime_seed).q, j.seed) if j.op == "axpy" else None
+            dicts.append({"op": j.op, "ctx": self.ctx.get(j.width, j.prime_seed), "n": j.n, "a": a, "b": b,
+                          "out": out, "alpha": alpha})
+        h = moma.moma_batch_create(dicts)
+        moma.moma_batch_run(h, st)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(st)
+        if self.keep:
+            for j, o in zip(jobs, outs):
+                self.outputs[j.seed] = o
+        return {"batch": h, "event": ev, "stream": sid, "outs": outs}
+
+    def poll(self, handle):
+        if not handle["event"].query():
+            return None
+        self.moma.moma_batch_destroy(handle["batch"])
+        self.free_streams.append(handle["stream"])
+        return self.t_base + self.base.elapsed_time(handle["event"]) * 1e-3
+
+
+def served_jobs(n_jobs=10000, seed=0, rate_per_s=1000.0):
+    """The served stream: transforms at 256/384 bits (768-bit transforms are not built in this
+    version, so 768-bit requests are vector ops), vectors at 256/384/768 bits."""
+    arrivals, jobs = inputs.served_stream(n_jobs=n_jobs, seed=seed, rate_per_s=rate_per_s)
+    out = []
+    for j in jobs:
+        if j.width == 768 and j.op in ("ntt_fwd", "ntt_inv"):
+            lg = int(np.log2(j.n)) + 2  # same seed-derived size range shifted into the vector range
+            j = inputs.Job(op="mul" if j.op == "ntt_fwd" else "axpy", width=768, n=1 << min(max(lg, 16), 24),
+                           seed=j.seed, prime_seed=j.prime_seed)
+        out.append(j)
+    return arrivals, out
+
+
+def serve(arrivals, jobs, contexts, slots=4, budget_bytes=BUDGET_BYTES, max_batch_jobs=64, executor=None):
+    ex = executor or GpuExecutor(contexts, slots=slots)
+    sched = Scheduler(ex, budget_bytes=budget_bytes, slots=slots, max_batch_jobs=max_batch_jobs)
+    return sched.run(arrivals, jobs)

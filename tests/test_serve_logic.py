@@ -1,0 +1,81 @@
+"""Host logic of the server (admission by memory budget, slots, FIFO, latencies) with a fake
+executor: no GPU involved."""
+import time
+
+from paper_2501_07535_gb300 import inputs, serve
+
+
+class FakeExecutor:
+    """Each batch takes `per_job_s` per job; completion is visible once the host clock passes it."""
+
+    def __init__(self, per_job_s=2e-4, footprint=lambda j: j.n):
+        self.per_job = per_job_s
+        self.fp = footprint
+        self.launches = []
+
+    def start(self, t0):
+        self.t0 = t0
+
+    def footprint(self, job):
+        return self.fp(job)
+
+    def launch(self, jobs):
+        now = time.perf_counter() - self.t0
+        done = now + self.per_job * len(jobs)
+        self.launches.append((now, done, [j.seed for j in jobs]))
+        return done
+
+    def poll(self, handle):
+        return handle if time.perf_counter() - self.t0 >= handle else None
+
+
+def _jobs(n, size=100):
+    return [inputs.Job(op="mul", width=256, n=size, seed=i) for i in range(n)]
+
+
+def test_all_jobs_complete_fifo_and_latency_nonnegative():
+    jobs = _jobs(300)
+    arrivals = [i * 1e-4 for i in range(300)]
+    ex = FakeExecutor()
+    st = serve.Scheduler(ex, budget_bytes=10**9, slots=3, max_batch_jobs=16).run(arrivals, jobs)
+    assert st.completed == 300 and st.rejected == 0
+    assert all(lat >= -1e-9 for lat in st.latencies_s)
+    order = [s for _, _, seeds in ex.launches for s in seeds]
+    assert order == sorted(order)  # admitted in arrival order
+    assert st.max_concurrent_batches <= 3
+
+
+def test_budget_is_respected_and_oversize_rejected():
+    jobs = _jobs(40, size=100) + [inputs.Job(op="mul", width=256, n=10**6, seed=99)]
+    arrivals = [0.0] * len(jobs)
+    ex = FakeExecutor()
+    sched = serve.Scheduler(ex, budget_bytes=450, slots=4, max_batch_jobs=64)
+    st = sched.run(arrivals, jobs)
+    assert st.rejected == 1 and sched.rejected == [40]
+    assert st.completed == 40
+    assert st.max_inflight_bytes <= 450
+    assert all(len(seeds) <= 4 for _, _, seeds in ex.launches)  # 4 jobs of 100 fit the budget
+
+
+def test_continuous_batching_admits_while_others_run():
+    jobs = _jobs(200)
+    arrivals = [i * 5e-5 for i in range(200)]
+    ex = FakeExecutor(per_job_s=1e-3)
+    st = serve.Scheduler(ex, budget_bytes=10**9, slots=4, max_batch_jobs=8).run(arrivals, jobs)
+    assert st.completed == 200
+    assert st.max_concurrent_batches >= 2
+    # some batch was launched while an earlier one was still running
+    overlaps = sum(1 for k in range(1, len(ex.launches)) if ex.launches[k][0] < ex.launches[k - 1][1])
+    assert overlaps > 0
+
+
+def test_served_stream_shape():
+    arrivals, jobs = serve.served_jobs(n_jobs=2000, seed=0, rate_per_s=1000.0)
+    assert len(jobs) == 2000 and arrivals == sorted(arrivals)
+    assert abs(arrivals[-1] / 2000 - 1e-3) < 2e-4  # Poisson rate
+    assert {j.width for j in jobs} == {256, 384, 768}
+    for j in jobs:
+        if j.op in ("ntt_fwd", "ntt_inv"):
+            assert j.width in (256, 384) and 1 << 12 <= j.n <= 1 << 22
+        else:
+            assert j.op in ("mul", "axpy") and 1 << 16 <= j.n <= 1 << 24
