@@ -160,16 +160,13 @@ class ClockSampler:
 def run_ours(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    from paper_2501_07535_gb300 import build, inputs, moma
+    from paper_2501_07535_gb300 import build, inputs, moma, replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replicas.world()
     if world > 1:
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        replicas.init("nccl")
 
     # CPU oracle pool: spawned before any GPU work (rank 0 only)
     pool = None
@@ -189,16 +186,11 @@ def run_ours(args):
     sms = props.multi_processor_count
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dev)
 
     # ---- inputs (resident in HBM)
     xs = np.stack([inputs.residues(q, L, n, seed=10 + t + 100 * rank) for t in range(NTT_BATCH)])
@@ -255,22 +247,39 @@ def run_ours(args):
     mul_ms = max_over_ranks(m0.elapsed_time(m1))
     gelem = world * VEC_N * args.steps / (mul_ms * 1e-3) / 1e9
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
-    hx = torch.from_numpy(xs.view(np.int32)).pin_memory()
-    hy = torch.empty_like(hx).pin_memory()
-    for _ in range(max(1, args.warmup)):
-        dx.copy_(hx, non_blocking=True)
-        ntt_step()
-        hy.copy_(dy, non_blocking=True)
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region:
+    # two streams alternate steps, so the host->device copy of one step overlaps the
+    # transforms of the previous one (copy engines and SMs work at the same time)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hx = [torch.from_numpy(xs.view(np.int32)).pin_memory() for _ in range(2)]
+    hy = [torch.empty_like(hx[0]).pin_memory() for _ in range(2)]
+    dxs = [dx, torch.empty_like(dx)]
+    dys = [dy, torch.empty_like(dy)]
+
+    def e2e_step(i):
+        k = i % 2
+        s_ = streams[k]
+        with torch.cuda.stream(s_):
+            dxs[k].copy_(hx[k], non_blocking=True)
+            moma.moma_ntt_fwd_many(ctx, n, NTT_BATCH, dxs[k], dys[k], s_)
+            hy[k].copy_(dys[k], non_blocking=True)
+
+    for i in range(max(2, args.warmup)):
+        e2e_step(i)
     barrier()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(st)
-    for _ in range(args.steps):
-        dx.copy_(hx, non_blocking=True)
-        ntt_step()
-        hy.copy_(dy, non_blocking=True)
+    for s_ in streams:
+        s_.wait_event(t0)
+    for i in range(args.steps):
+        e2e_step(i)
+    for s_ in streams:
+        ev_ = torch.cuda.Event()
+        ev_.record(s_)
+        st.wait_event(ev_)
     t1.record(st)
     barrier()
+    assert torch.equal(hy[(args.steps - 1) % 2], dys[(args.steps - 1) % 2].cpu())
     e2e_ms = max_over_ranks(t0.elapsed_time(t1))
     clk.__exit__(None, None, None)
     clocks = clk.summary()
@@ -288,9 +297,10 @@ def run_ours(args):
     mul_prod = word_products_per_mulmod(L) * VEC_N
     mul_s = mul_ms * 1e-3 / args.steps
     mul_roof_s = max(mul_bytes / (hbm * 1e9) if hbm else 0.0, mul_prod / prod_peak)
-    launches = args.steps * (n_pass_launches + 1)
+    launches = args.steps * n_pass_launches  # pass kernels in the timed NTT region
     c4 = run_uneven_batch(max(3, args.steps // 2), 2)
     c5 = run_served(n_jobs=args.serve_jobs) if args.serve_jobs > 0 else None
+    sens = run_sensitivity()
 
     result = {
         "metric": METRIC,
@@ -317,6 +327,7 @@ def run_ours(args):
                      "algorithmic": f"(n/2)log2(n) mulmods x (2L^2+L) = {word_products_per_mulmod(L)} word "
                                     f"products per mulmod, {NTT_BATCH} transforms per step"},
         "mulmod": {"value": round(gelem, 3), "unit": "Gelem/s", "ms_per_step": round(mul_ms / args.steps, 4),
+                   "gpu_launches": args.steps,
                    "roofline": {"bound": "hbm" if mul_bytes / (hbm * 1e9 if hbm else 1) >= mul_prod / prod_peak
                                 else "alu",
                                 "time_us": round(mul_roof_s * 1e6, 2), "achieved_us": round(mul_s * 1e6, 2),
@@ -326,6 +337,7 @@ def run_ours(args):
                                 "products_t_peak": round(peak_t, 3)}},
         "batched_vs_plain": c4,
         "served": c5,
+        "sensitivity": sens,
         "e2e": {"value": round(e2e, 2), "unit": "NTT/s", "h2d_bytes_per_step": step_bytes,
                 "d2h_bytes_per_step": step_bytes},
         "gpu_launches": launches,
@@ -346,12 +358,12 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     moma.moma_ctx_destroy(ctx)
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finalize()
 
 
 def run_profile(args):
-    """Small case for ncu captures: only batched forward NTTs (plan set-up call first)."""
+    """Small cases for ncu captures: batched forward NTTs (plan set-up call first), or the
+    2^24-element mulmod."""
     import numpy as np
     import torch
 
@@ -360,6 +372,16 @@ def run_profile(args):
     q = inputs.prime(WIDTH).q
     n = 1 << LOGN
     ctx = moma.moma_ctx_create(q, WIDTH)
+    if args.profile_op == "mul":
+        a = moma.to_device(inputs.residues(q, L, VEC_N, seed=1))
+        b = moma.to_device(inputs.residues(q, L, VEC_N, seed=2))
+        c = torch.empty_like(a)
+        for _ in range(1 + args.steps):
+            moma.moma_vec_mulmod(ctx, VEC_N, a, b, c)
+        torch.cuda.synchronize()
+        moma.moma_ctx_destroy(ctx)
+        print(json.dumps({"profile": "vec_mulmod", "n": VEC_N, "calls": 1 + args.steps}))
+        return
     xs = np.stack([inputs.residues(q, L, n, seed=10 + t) for t in range(args.ntt_batch)])
     dx = moma.to_device(xs)
     dy = torch.empty_like(dx)
@@ -423,6 +445,55 @@ def run_uneven_batch(steps, warmup, n_jobs=256, seed=0):
     finally:
         js.close()
         js.ctx.close()
+
+
+def run_sensitivity(steps=5):
+    """Sec. 5.4 analogues: (1) forward NTT runtime against width at n = 4096 (batches of 256,
+    ns per butterfly = 2t/(n log2 n) as in Sec. 5.3); (2) mulmod with schoolbook carry chains,
+    whole mad.wide products and Karatsuba (Eq. mulk) at each width, 2^22 elements."""
+    import torch
+
+    from paper_2501_07535_gb300 import inputs, moma
+    out = {"ntt_n4096": [], "mulmod_engines": []}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    prev = None
+    for w in (128, 256, 384, 768):
+        p = inputs.prime(w)
+        ctx = moma.moma_ctx_create(p.q, w)
+        n, cnt = 4096, 256
+        x = torch.zeros((cnt, p.L, n), dtype=torch.int32, device="cuda")
+        x[:, 0, :] = 3  # canonical
+        y = torch.empty_like(x)
+        ms = timed(lambda: moma.moma_ntt_fwd_many(ctx, n, cnt, x, y))
+        ns_bfly = ms * 1e6 / cnt * 2 / (n * 12)
+        row = {"bits": w, "ms_per_256": round(ms, 4), "ns_per_butterfly": round(ns_bfly, 4),
+               "slowdown_vs_previous_width": round(ns_bfly / prev, 2) if prev else None}
+        prev = ns_bfly
+        out["ntt_n4096"].append(row)
+        vn = 1 << 22
+        a = moma.to_device(inputs.residues(p.q, p.L, vn, 1))
+        b = moma.to_device(inputs.residues(p.q, p.L, vn, 2))
+        c = torch.empty_like(a)
+        eng = {}
+        for e, name in ((1, "schoolbook_carry"), (2, "schoolbook_wide"), (3, "karatsuba")):
+            moma.moma_ctx_set_config(ctx, "mul", vn, engine=e, vec_width=1)
+            eng[name] = round(vn / timed(lambda: moma.moma_vec_mulmod(ctx, vn, a, b, c)) / 1e6, 2)
+        out["mulmod_engines"].append({"bits": w, "gelem_s": eng,
+                                      "karatsuba_over_schoolbook": round(eng["karatsuba"] / eng["schoolbook_carry"], 3)})
+        moma.moma_ctx_destroy(ctx)
+    return out
 
 
 def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
@@ -499,6 +570,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small NTT-only case for ncu captures")
     ap.add_argument("--ntt-batch", type=int, default=8)
+    ap.add_argument("--profile-op", default="ntt", choices=["ntt", "mul"])
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

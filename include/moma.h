@@ -15,7 +15,8 @@
  * Widths.  bits in {128, 256, 384, 768}; L = bits/32 limbs of 32 bits.  The modulus
  *   q must be odd and have exactly bits-4 bits (Sec. 5.2: a (k-4)-bit modulus for a
  *   k-bit container, which the Barrett constants of Sec. 3.1 need); otherwise
- *   MOMA_ERR_MODULUS.
+ *   MOMA_ERR_MODULUS.  Every width is supported by every call, except transform jobs inside
+ *   batches (128 to 384 bits) and moma_ntt_fwd_noalloc (128 to 384 bits).
  * Layout.  A vector of n residues is limb-major: uint32 v[L][n], limb 0 the least
  *   significant word of each residue (the paper writes words most significant first;
  *   that is notation only).  Plane j of element i is at v[j*n + i].
@@ -158,7 +159,8 @@ moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, ui
  * (out = a * b mod (x^n - 1, q)), MOMA_OP_ADD / SUB / MUL (out = a op b), MOMA_OP_AXPY
  * (out = alpha * a + b, alpha a HOST array of L limbs).  Device vectors follow the
  * conventions above; each job uses its own context (any widths and moduli may be mixed;
- * transforms at 128 to 384 bits, vector ops at every width). */
+ * transforms at 128 to 384 bits, vector ops at every width; a 768-bit transform job gives
+ * MOMA_ERR_UNSUPPORTED, use the per-call transforms for those). */
 typedef struct {
   int op;
   moma_ctx *ctx;
@@ -221,8 +223,11 @@ typedef enum {
 
 /* Schedule of one operation at one size.  Any field set to 0 means "library default".
  *   engine     1: word products as mad.lo/mad.hi carry chains (mad.lo.cc, madc.hi.cc);
- *              2: word products as mad.wide (whole 64-bit products, carry in the addend).
- *              Both compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd).
+ *              2: word products as mad.wide (whole 64-bit products, carry in the addend);
+ *              3: (MOMA_OP_MUL only) the double-width product a*b by Karatsuba (Sec. 2.2
+ *              Eq. mulk) down to 4-limb carry-chain schoolbook products.
+ *              1 and 2 compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd);
+ *              all engines give identical results.
  *   tile_log   transforms: log2 of the elements one CTA holds in shared memory.
  *   max_logr   transforms: largest radix (log2) of one Stockham pass.
  *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment).

@@ -150,7 +150,6 @@ static moma_status ntt_call(moma_ctx* ctx, size_t n, size_t count, bool inverse,
   if (!aligned4(in) || !aligned4(out)) return MOMA_ERR_ALIGN;
   int lg = log2_exact(n);
   if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-  if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
   if (count > ((size_t)1 << 20)) return MOMA_ERR_SIZE;
   return launch_ntt(ctx, lg, count, inverse, in, out, (cudaStream_t)stream);
 }
@@ -178,7 +177,6 @@ moma_status moma_polymul(moma_ctx* ctx, size_t n, const uint32_t* a, const uint3
   if (!aligned4(a) || !aligned4(b) || !aligned4(c)) return MOMA_ERR_ALIGN;
   int lg = log2_exact(n);
   if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-  if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
   return launch_polymul(ctx, lg, a, b, c, (cudaStream_t)stream);
 }
 

@@ -327,6 +327,8 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     }
     const int lg = log2_n(jb.n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
+    // 768-bit transform tiles would raise the persistent kernel's register budget (and cut
+    // the occupancy of every other tile); 768-bit transforms run through the per-call API
     if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
     moma_config cfg = ntt_config(ctx, jb.op, lg);
     const int tl = std::min(cfg.tile_log, kBatchTileLog);

@@ -42,7 +42,10 @@ struct VecT<4> {
   static __device__ __forceinline__ T join(const uint32_t* o) { return make_uint4(o[0], o[1], o[2], o[3]); }
 };
 
-template <int L, int OP, int V, bool WIDE>
+// ENG: 1 carry-chain rows, 2 whole-product (mad.wide) rows, 3 Karatsuba double-width product
+// (Eq. mulk, carry-chain base) for mulmod; axpy's fixed-scalar product has no double-width
+// product, so ENG 3 uses carry chains there.
+template <int L, int OP, int V, int ENG>
 __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArgs<L> p) {
   using VT = typename VecT<V>::T;
   const uint64_t units = p.n / V;
@@ -67,10 +70,10 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
       } else if constexpr (OP == VEC_SUB) {
         submod<L>(z[v], x[v], y[v], p.k.q);
       } else if constexpr (OP == VEC_MUL) {
-        mulmod_barrett<L, WIDE>(z[v], x[v], y[v], p.k);
+        mulmod_barrett<L, ENG == 2, ENG == 3>(z[v], x[v], y[v], p.k);
       } else {
         uint32_t ax[L];
-        mulmod_fixed<L, WIDE>(ax, x[v], p.alpha, p.alphap, p.k);
+        mulmod_fixed<L, ENG == 2>(ax, x[v], p.alpha, p.alphap, p.k);
         addmod<L>(z[v], ax, y[v], p.k.q);
       }
     }
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
   }
 }
 
-template <int L, int OP, int V, bool WIDE>
+template <int L, int OP, int V, int ENG>
 static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                            const uint32_t* alpha_host, cudaStream_t st) {
   VecArgs<L> p;
@@ -110,7 +113,7 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
   static int occ = -1;  // per-instantiation occupancy, computed once
   if (occ < 0) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V, WIDE>, 256, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V, ENG>, 256, 0) != cudaSuccess)
       return MOMA_ERR_CUDA;
     occ = o > 0 ? o : 1;
   }
@@ -119,7 +122,7 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
   const uint64_t cap = (uint64_t)ctx->num_sms * (uint64_t)occ;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) return MOMA_OK;
-  vec_kernel<L, OP, V, WIDE><<<(unsigned)blocks, 256, 0, st>>>(p);
+  vec_kernel<L, OP, V, ENG><<<(unsigned)blocks, 256, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
 }
 
@@ -143,32 +146,33 @@ moma_config vec_config(const moma_ctx* ctx, int vec_op) {
   return c;
 }
 
-template <int L, int OP, bool WIDE>
+template <int L, int OP, int ENG>
 static moma_status dispatch_v(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                               const uint32_t* alpha, int vw, cudaStream_t st) {
   constexpr int VM = L <= 8 ? 4 : (L <= 12 ? 2 : 1);
   const uintptr_t mis = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c;
   if (VM >= 4 && vw >= 4 && n % 4 == 0 && (mis & 15) == 0)
-    return run_vec<L, OP, (VM >= 4 ? 4 : 1), WIDE>(ctx, n, a, b, c, alpha, st);
+    return run_vec<L, OP, (VM >= 4 ? 4 : 1), ENG>(ctx, n, a, b, c, alpha, st);
   if (VM >= 2 && vw >= 2 && n % 2 == 0 && (mis & 7) == 0)
-    return run_vec<L, OP, (VM >= 2 ? 2 : 1), WIDE>(ctx, n, a, b, c, alpha, st);
-  return run_vec<L, OP, 1, WIDE>(ctx, n, a, b, c, alpha, st);
+    return run_vec<L, OP, (VM >= 2 ? 2 : 1), ENG>(ctx, n, a, b, c, alpha, st);
+  return run_vec<L, OP, 1, ENG>(ctx, n, a, b, c, alpha, st);
 }
 
 template <int L>
 static moma_status dispatch_op(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                                const uint32_t* alpha, const moma_config& cfg, cudaStream_t st) {
-  const bool wide = cfg.engine == 2;
+  const int eng = cfg.engine;
   const int vw = cfg.vec_width;
   switch (op) {
-    case VEC_ADD: return dispatch_v<L, VEC_ADD, false>(ctx, n, a, b, c, alpha, vw, st);
-    case VEC_SUB: return dispatch_v<L, VEC_SUB, false>(ctx, n, a, b, c, alpha, vw, st);
+    case VEC_ADD: return dispatch_v<L, VEC_ADD, 1>(ctx, n, a, b, c, alpha, vw, st);
+    case VEC_SUB: return dispatch_v<L, VEC_SUB, 1>(ctx, n, a, b, c, alpha, vw, st);
     case VEC_MUL:
-      return wide ? dispatch_v<L, VEC_MUL, true>(ctx, n, a, b, c, alpha, vw, st)
-                  : dispatch_v<L, VEC_MUL, false>(ctx, n, a, b, c, alpha, vw, st);
+      return eng == 2 ? dispatch_v<L, VEC_MUL, 2>(ctx, n, a, b, c, alpha, vw, st)
+             : eng == 3 ? dispatch_v<L, VEC_MUL, 3>(ctx, n, a, b, c, alpha, vw, st)
+                        : dispatch_v<L, VEC_MUL, 1>(ctx, n, a, b, c, alpha, vw, st);
     case VEC_AXPY:
-      return wide ? dispatch_v<L, VEC_AXPY, true>(ctx, n, a, b, c, alpha, vw, st)
-                  : dispatch_v<L, VEC_AXPY, false>(ctx, n, a, b, c, alpha, vw, st);
+      return eng == 2 ? dispatch_v<L, VEC_AXPY, 2>(ctx, n, a, b, c, alpha, vw, st)
+                      : dispatch_v<L, VEC_AXPY, 1>(ctx, n, a, b, c, alpha, vw, st);
   }
   return MOMA_ERR_INVALID_ARG;
 }

@@ -323,6 +323,74 @@ MOMA_DEV void mul_hi_trunc_w(uint32_t (&H)[L], const uint32_t (&x)[L], const uin
   for (int k = 0; k < L; ++k) H[k] = A[k + 1];
 }
 
+// ------------------------------------------------------------------ Eq. mulk (Karatsuba)
+// t = x * y with three half-size products per level (Sec. 2.2, Eq. mulk):
+//   x = x1 z + x0, y = y1 z + y0, z = 2^(32 L/2)
+//   p0 = x0 y0, p2 = x1 y1, p1 = (x0 + x1)(y0 + y1), t = p0 + (p1 - p0 - p2) z + p2 z^2.
+// The half sums carry one extra bit each (cx, cy): p1 = sx sy + (cx sy + cy sx) z + cx cy z^2.
+// Recursion stops at KBASE limbs (schoolbook carry chains) or at an odd limb count.
+constexpr int kKaratsubaBase = 4;
+
+template <int L>
+MOMA_DEV void mul_full_k(uint32_t (&t)[2 * L], const uint32_t (&x)[L], const uint32_t (&y)[L]) {
+  if constexpr (L <= kKaratsubaBase || (L % 2) != 0) {
+    mul_full<L>(t, x, y);
+  } else {
+    constexpr int H = L / 2;
+    uint32_t x0[H], x1[H], y0[H], y1[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      x0[i] = x[i];
+      x1[i] = x[H + i];
+      y0[i] = y[i];
+      y1[i] = y[H + i];
+    }
+    uint32_t p0[2 * H], p2[2 * H];
+    mul_full_k<H>(p0, x0, y0);
+    mul_full_k<H>(p2, x1, y1);
+    uint32_t sx[H], sy[H];
+    add_words<H, false>(sx, x0, x1);
+    const uint32_t cx = carry_out();
+    add_words<H, false>(sy, y0, y1);
+    const uint32_t cy = carry_out();
+    uint32_t p1[2 * H + 1];
+    {
+      uint32_t pl[2 * H];
+      mul_full_k<H>(pl, sx, sy);
+#pragma unroll
+      for (int i = 0; i < 2 * H; ++i) p1[i] = pl[i];
+    }
+    p1[2 * H] = cx & cy;
+    // p1 += (cx ? sy : 0) z + (cy ? sx : 0) z
+    uint32_t m[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) m[i] = sy[i] & (0u - cx);
+    add_words<H, false>(p1 + H, p1 + H, m);
+    p1[2 * H] = addc(p1[2 * H], 0u);
+#pragma unroll
+    for (int i = 0; i < H; ++i) m[i] = sx[i] & (0u - cy);
+    add_words<H, false>(p1 + H, p1 + H, m);
+    p1[2 * H] = addc(p1[2 * H], 0u);
+    // mid = p1 - p0 - p2 (non-negative, 2H+1 words)
+    sub_words<2 * H, false>(p1, p1, p0);
+    p1[2 * H] = subc(p1[2 * H], 0u);
+    sub_words<2 * H, false>(p1, p1, p2);
+    p1[2 * H] = subc(p1[2 * H], 0u);
+    // t = p0 + mid z + p2 z^2
+#pragma unroll
+    for (int i = 0; i < 2 * H; ++i) {
+      t[i] = p0[i];
+      t[2 * H + i] = p2[i];
+    }
+    add_words<2 * H + 1, false>(t + H, t + H, p1);
+    if constexpr (H > 1) {
+#pragma unroll
+      for (int i = 3 * H + 1; i < 4 * H - 1; ++i) t[i] = addc_cc(t[i], 0u);
+      t[4 * H - 1] = addc(t[4 * H - 1], 0u);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ per-modulus constants
 // Kernel-parameter copy of the constants of one modulus (lives in the constant bank).
 template <int L>
@@ -369,12 +437,14 @@ MOMA_DEV uint32_t barrett_reduce(uint32_t (&c)[L], uint32_t (&s)[L], const uint3
   return ~keep & 1u;
 }
 
-// c = a * b mod q (Eq. barrett).  WIDE selects the whole-product rows.
-template <int L, bool WIDE = false>
+// c = a * b mod q (Eq. barrett).  WIDE selects the whole-product rows; KARA forms the double
+// width product a*b by Karatsuba (Eq. mulk) instead of schoolbook (Eq. muls).
+template <int L, bool WIDE = false, bool KARA = false>
 MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
                              const ModK<L>& k) {
   uint32_t t[2 * L];
-  if constexpr (WIDE) mul_full_w<L>(t, a, b);
+  if constexpr (KARA) mul_full_k<L>(t, a, b);
+  else if constexpr (WIDE) mul_full_w<L>(t, a, b);
   else mul_full<L>(t, a, b);
   uint32_t s[L];
   barrett_reduce<L, WIDE>(c, s, t, k);

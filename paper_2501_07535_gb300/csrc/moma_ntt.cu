@@ -45,8 +45,9 @@ int max_tile_log(int L) {
 }
 
 // Measured on GB300 (2^20-point transforms, 16 per call): whole-product rows are faster up to
-// 256 bits, carry chains at 384 bits.
-static int default_engine(int L) { return L <= 8 ? 2 : 1; }
+// 256 bits, carry chains at 384 bits; at 768 bits only whole-product rows fit the registers
+// without spilling.
+static int default_engine(int L) { return L == 12 ? 1 : 2; }
 
 moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
   moma_config c = {0, 0, 0, 0, 0};
@@ -165,6 +166,7 @@ static moma_status gen_table_l(const moma_ctx* ctx, uint32_t* dst, uint64_t coun
     case 4: return gen_table<4>(ctx, dst, count, D, C, S, logn, pw);
     case 8: return gen_table<8>(ctx, dst, count, D, C, S, logn, pw);
     case 12: return gen_table<12>(ctx, dst, count, D, C, S, logn, pw);
+    case 24: return gen_table<24>(ctx, dst, count, D, C, S, logn, pw);
   }
   return MOMA_ERR_UNSUPPORTED;
 }
@@ -336,6 +338,8 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
                         : run_pass<8, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
     case 12: return wide ? run_pass<12, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
                          : run_pass<12, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    case 24: return wide ? run_pass<24, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                         : run_pass<24, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   }
   return MOMA_ERR_UNSUPPORTED;
 }

@@ -32,7 +32,7 @@ extern "C" moma_status moma_ctx_set_config(moma_ctx* ctx, int op, size_t n, cons
     return MOMA_OK;
   }
   if (is_vec_op(op)) {
-    if (cfg->engine < 0 || cfg->engine > 2) return MOMA_ERR_INVALID_ARG;
+    if (cfg->engine < 0 || cfg->engine > 3) return MOMA_ERR_INVALID_ARG;
     if (cfg->vec_width != 0 && cfg->vec_width != 1 && cfg->vec_width != 2 && cfg->vec_width != 4)
       return MOMA_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->lock);
@@ -85,7 +85,6 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   std::vector<moma_config> cands;
   int lg = -1;
   if (is_ntt_op(op)) {
-    if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
     lg = log2_of(n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
     if (count == 0) count = 1;
@@ -106,8 +105,8 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
         }
   } else if (is_vec_op(op)) {
     if (n == 0) return MOMA_ERR_SIZE;
-    const bool mul = op == MOMA_OP_MUL || op == MOMA_OP_AXPY;
-    for (int engine = 1; engine <= (mul ? 2 : 1); ++engine)
+    const int engines = op == MOMA_OP_MUL ? 3 : (op == MOMA_OP_AXPY ? 2 : 1);
+    for (int engine = 1; engine <= engines; ++engine)
       for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v, 0});
   } else {
     return MOMA_ERR_INVALID_ARG;
