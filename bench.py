@@ -36,6 +36,12 @@ VEC_N = 1 << 24
 L = WIDTH // 32
 
 
+# DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20)
+# from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule.
+NTT_PASS_TRAFFIC_BYTES = 969.7e6
+NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 2, "tile_log": 10, "max_logr": 5, "vec_width": 0, "cta_threads": 128}
+
+
 def word_products_per_mulmod(L):
     """Algorithmic 32x32->64 word products of one L-limb modular multiplication: 2L^2 + L."""
     return 2 * L * L + L
@@ -321,7 +327,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (512 MiB per NTT step, 1.5 GiB per mulmod step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": round(ntt_achieved, 3), "peak": round(peak_t, 3),
-                     "unit": "T word-products/s", "frac": round(ntt_achieved / peak_t, 4), "traffic": None,
+                     "unit": "T word-products/s", "frac": round(ntt_achieved / peak_t, 4),
+                     "traffic": NTT_PASS_TRAFFIC_BYTES if ntt_cfg == NTT_PASS_TRAFFIC_SCHEDULE else None,
                      "peak_source": "measured in this run by moma_probe_imad: fastest 32x32->64 product form "
                                     "(mad.wide) on all SMs",
                      "algorithmic": f"(n/2)log2(n) mulmods x (2L^2+L) = {word_products_per_mulmod(L)} word "
