@@ -37,9 +37,10 @@ L = WIDTH // 32
 
 
 # DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20)
-# from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule.
-NTT_PASS_TRAFFIC_BYTES = 969.7e6
-NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 2, "tile_log": 10, "max_logr": 5, "vec_width": 0, "cta_threads": 128}
+# from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule
+# and kernel version (None otherwise).
+NTT_PASS_TRAFFIC_BYTES = None
+NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 1, "tile_log": 10, "max_logr": 5, "vec_width": 0, "cta_threads": 128}
 
 
 def word_products_per_mulmod(L):

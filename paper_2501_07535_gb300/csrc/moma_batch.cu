@@ -92,7 +92,7 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __restrict__ segs, uint32_t nseg,
                                                              uint32_t total, uint32_t* ctr, int* status,
                                                              uint64_t wait_polls) {
-  extern __shared__ uint32_t sm[];
+  extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t s_tile, s_seg, s_skip;
   for (;;) {
     if (threadIdx.x == 0) {

@@ -21,7 +21,8 @@
 //
 // Twiddles are in the reduction's domain: every table entry w carries its companion
 // floor(w * 2^(32L) / q), so a twiddle multiplication needs no double-width product
-// (mulmod_fixed).  Tables are built on the device once per (modulus, size, direction).
+// (mulmod_fixed).  Tables are built on the device once per (modulus, size, direction) and
+// stored entry-major, [entry][w limbs | companion limbs], 16-byte aligned per entry.
 #include <algorithm>
 
 #include "moma_internal.hpp"
@@ -32,10 +33,22 @@ namespace moma {
 
 constexpr int kNttMaxThreads = 256;  // per CTA; the launch may use 32, 64, 128 or 256
 
-// Default CTA tile (elements): 2^10 elements for 128 threads (L*4 KiB of shared memory);
-// measured best on GB300 for 128- to 384-bit transforms of 2^12 and 2^20 points.
-int default_tile_log(int L) { return L <= 12 ? 10 : 9; }
-constexpr int kDefaultThreads = 128;
+// Default schedule per width, the fastest measured on GB300 for 2^20-point transforms in
+// batches (see the autotuner for other sizes): 128-thread CTAs on 2^10-element tiles with radix
+// up to 2^5 through 384 bits, 256-thread CTAs on 2^11 tiles with radix 2^7 at 768 bits;
+// whole-product rows at 128 bits, carry chains above.
+struct NttDefaults {
+  int engine, tile_log, max_logr, threads;
+};
+static NttDefaults ntt_defaults(int L) {
+  switch (L) {
+    case 4: return {2, 10, 5, 128};
+    case 8: return {1, 10, 5, 128};
+    case 12: return {1, 10, 5, 128};
+    default: return {1, 11, 7, 256};
+  }
+}
+int default_tile_log(int L) { return ntt_defaults(L).tile_log; }
 
 // Largest tile that fits the 227 KiB of shared memory one CTA may use.
 int max_tile_log(int L) {
@@ -44,19 +57,15 @@ int max_tile_log(int L) {
   return t;
 }
 
-// Measured on GB300 (2^20-point transforms, 16 per call): whole-product rows are faster up to
-// 256 bits, carry chains at 384 bits; at 768 bits only whole-product rows fit the registers
-// without spilling.
-static int default_engine(int L) { return L == 12 ? 1 : 2; }
-
 moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
   moma_config c = {0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(op, logn));
   if (it != ctx->configs.end()) c = it->second;
-  if (c.engine == 0) c.engine = default_engine(ctx->L);
-  if (c.tile_log == 0) c.tile_log = default_tile_log(ctx->L);
-  if (c.max_logr == 0) c.max_logr = c.tile_log > 6 ? c.tile_log - 5 : 1;  // >= 32 groups per tile
-  if (c.cta_threads == 0) c.cta_threads = kDefaultThreads;
+  const NttDefaults d = ntt_defaults(ctx->L);
+  if (c.engine == 0) c.engine = d.engine;
+  if (c.tile_log == 0) c.tile_log = d.tile_log;
+  if (c.max_logr == 0) c.max_logr = c.tile_log == d.tile_log ? d.max_logr : (c.tile_log > 6 ? c.tile_log - 5 : 1);
+  if (c.cta_threads == 0) c.cta_threads = d.threads;
   c.vec_width = 0;
   return c;
 }
@@ -72,9 +81,12 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
   return true;
 }
 
+// Register cap: 128 per thread up to 384 bits (two 256-thread CTAs per SM at least); the
+// 768-bit kernel needs the full 255.
 template <int L, bool WIDE>
-__global__ void __launch_bounds__(kNttMaxThreads) ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
-  extern __shared__ uint32_t sm[];
+__global__ void __launch_bounds__(kNttMaxThreads, L <= 12 ? 2 : 1) ntt_pass_kernel(
+    const __grid_constant__ NttPassArgs<L> p) {
+  extern __shared__ __align__(16) uint32_t sm[];
   ntt_tile<L, WIDE>(p, blockIdx.x, sm);
 }
 
@@ -122,8 +134,8 @@ __global__ void __launch_bounds__(256) twiddle_gen_kernel(const __grid_constant_
     }
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      p.dst[idx + (uint64_t)l * p.count] = acc[l];
-      p.dst[idx + (uint64_t)(L + l) * p.count] = wp[l];
+      p.dst[idx * 2 * L + l] = acc[l];
+      p.dst[idx * 2 * L + L + l] = wp[l];
     }
   }
 }

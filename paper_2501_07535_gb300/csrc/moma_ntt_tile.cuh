@@ -6,10 +6,58 @@
 
 namespace moma {
 
-// XOR swizzle of a word index inside one limb plane of the tile: flips the low five
-// bits by the next five, so that both row-wise and bit-reversed column-wise accesses
-// spread over the 32 banks.  A bijection on every aligned block of 32 words.
+// XOR swizzle of an element slot of the tile: flips the low five bits by the next five, so
+// that row-wise and bit-reversed column-wise accesses spread over the banks.  A bijection on
+// every aligned block of 32 slots.
 __device__ __forceinline__ uint32_t swz(uint32_t x) { return x ^ ((x >> 5) & 31u); }
+
+// The tile is element-major: slot x holds the L limbs of one element in L/4 16-byte chunks.
+// With an even chunk count the chunk index is flipped by bit 2 of the slot, so eight
+// consecutive slots (one quarter-warp of 128-bit accesses) hit eight different bank groups.
+template <int L>
+__device__ __forceinline__ uint32_t chunk_of(uint32_t x, int c) {
+  if constexpr ((L / 4) % 2 == 0) return (uint32_t)c ^ ((x >> 2) & 1u);
+  else return (uint32_t)c;
+}
+
+template <int L>
+__device__ __forceinline__ void tile_load(const uint32_t* sm, uint32_t x, uint32_t (&v)[L]) {
+  const uint4* p = reinterpret_cast<const uint4*>(sm) + x * (L / 4);
+#pragma unroll
+  for (int c = 0; c < L / 4; ++c) {
+    const uint4 t = p[chunk_of<L>(x, c)];
+    v[4 * c] = t.x;
+    v[4 * c + 1] = t.y;
+    v[4 * c + 2] = t.z;
+    v[4 * c + 3] = t.w;
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void tile_store(uint32_t* sm, uint32_t x, const uint32_t (&v)[L]) {
+  uint4* p = reinterpret_cast<uint4*>(sm) + x * (L / 4);
+#pragma unroll
+  for (int c = 0; c < L / 4; ++c) p[chunk_of<L>(x, c)] = make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
+// One twiddle entry (value and companion) from an entry-major table, L/2 16-byte loads.
+template <int L>
+__device__ __forceinline__ void twiddle_load(const uint32_t* table, uint64_t entry, uint32_t (&w)[L],
+                                             uint32_t (&wp)[L]) {
+  const uint4* p = reinterpret_cast<const uint4*>(table + entry * 2 * L);
+#pragma unroll
+  for (int c = 0; c < L / 4; ++c) {
+    const uint4 a = __ldg(p + c), b = __ldg(p + L / 4 + c);
+    w[4 * c] = a.x;
+    w[4 * c + 1] = a.y;
+    w[4 * c + 2] = a.z;
+    w[4 * c + 3] = a.w;
+    wp[4 * c] = b.x;
+    wp[4 * c + 1] = b.y;
+    wp[4 * c + 2] = b.z;
+    wp[4 * c + 3] = b.w;
+  }
+}
 
 template <int L>
 struct NttPassArgs {
@@ -35,7 +83,7 @@ enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4, F_LAST = 8 };
 // With MUL false the twiddle is 1.
 template <int L, bool WIDE>
 __device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&b)[L], bool mul,
-                                                   const uint32_t* twp, uint32_t tw_stride, const ModK<L>& k) {
+                                                   const uint32_t* table, uint32_t entry, const ModK<L>& k) {
   uint32_t x[L], d[L];
   add_words<L, false>(x, a, b);  // [0, 8q)
   cond_sub<L>(x, k.q4);           // [0, 4q)
@@ -43,11 +91,7 @@ __device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&
   sub_words<L, false>(d, d, b);   // a + 4q - b in (0, 8q)
   if (mul) {
     uint32_t w[L], wp[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      w[l] = __ldg(twp + l * tw_stride);
-      wp[l] = __ldg(twp + (L + l) * tw_stride);
-    }
+    twiddle_load<L>(table, entry, w, wp);
     mulmod_fixed_lazy<L, WIDE>(b, d, w, wp, k);  // [0, 3q)
   } else {
     cond_sub<L>(d, k.q4);
@@ -99,23 +143,16 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
     if ((p.flags & F_PRETW) && r != 0 && (j & ns_mask) != 0) {
       const uint64_t ti = (uint64_t)(r - 1) * (ns_mask + 1) + (j & ns_mask);
       uint32_t w[L], wp[L], t[L];
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        w[l] = __ldg(p.tw_pass + ti + (uint64_t)l * p.tw_count);
-        wp[l] = __ldg(p.tw_pass + ti + (uint64_t)(L + l) * p.tw_count);
-      }
+      twiddle_load<L>(p.tw_pass, ti, w, wp);
       mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
 #pragma unroll
       for (int l = 0; l < L; ++l) v[l] = t[l];
     }
-    const uint32_t a = swz(e);  // e = r*G + g
-#pragma unroll
-    for (int l = 0; l < L; ++l) sm[l * T + a] = v[l];
+    tile_store<L>(sm, swz(e), v);  // e = r*G + g
   }
   __syncthreads();
 
   // ---- R-point transforms: logR radix-2 DIF stages, in place in the tile
-  const uint32_t half_int = R >> 1;
 #pragma unroll 1
   for (uint32_t s = 0; s < p.logR; ++s) {
     const uint32_t logh = p.logR - s - 1;
@@ -126,18 +163,12 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
       const uint32_t p0 = (blk << (logh + 1)) + i;
       const uint32_t a0 = swz((p0 << p.logG) + g), a1 = swz(((p0 + h) << p.logG) + g);
       uint32_t x0[L], x1[L];
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        x0[l] = sm[l * T + a0];
-        x1[l] = sm[l * T + a1];
-      }
+      tile_load<L>(sm, a0, x0);
+      tile_load<L>(sm, a1, x1);
       // twiddle w_(2h)^i = w_R^(i * R/(2h)); 1 for i = 0 and in the last stage (h = 1)
-      dif_butterfly_lazy<L, WIDE>(x0, x1, i != 0, p.tw_int + (i << s), half_int, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        sm[l * T + a0] = x0[l];
-        sm[l * T + a1] = x1[l];
-      }
+      dif_butterfly_lazy<L, WIDE>(x0, x1, i != 0, p.tw_int, i << s, p.k);
+      tile_store<L>(sm, a0, x0);
+      tile_store<L>(sm, a1, x1);
     }
     __syncthreads();
   }
@@ -155,10 +186,8 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
     const uint64_t kk = j & ns_mask;
     const uint64_t addr = base + (j - kk) * R + kk + ((uint64_t)sp << p.logNs);
     const uint32_t pr = __brev(sp) >> (32 - p.logR);
-    const uint32_t a = swz((pr << p.logG) + g);
     uint32_t v[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) v[l] = sm[l * T + a];
+    tile_load<L>(sm, swz((pr << p.logG) + g), v);
     if (p.flags & F_LAST) {  // [0, 4q) -> [0, q)
       cond_sub<L>(v, p.k.q2);
       cond_sub<L>(v, p.k.q);
