@@ -133,7 +133,9 @@ moma_config vec_config(const moma_ctx* ctx, int vec_op) {
   moma_config c = {0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
   if (it != ctx->configs.end()) c = it->second;
-  if (c.engine == 0) c.engine = 1;
+  // Karatsuba (engine 3) measured at or above schoolbook at every width for mulmod on GB300
+  // (1.00x at 256 bits up to 1.13x at 768 bits); carry chains for the other ops
+  if (c.engine == 0) c.engine = vec_op == VEC_MUL ? 3 : 1;
   // measured on GB300 at 2^24 elements: multiplications prefer one element per thread from
   // 256 bits up, additions and axpy two; narrow widths take the widest vectors
   if (c.vec_width == 0) {

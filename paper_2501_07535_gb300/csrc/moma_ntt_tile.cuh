@@ -6,10 +6,13 @@
 
 namespace moma {
 
-// XOR swizzle of an element slot of the tile: flips the low five bits by the next five, so
-// that row-wise and bit-reversed column-wise accesses spread over the banks.  A bijection on
-// every aligned block of 32 slots.
-__device__ __forceinline__ uint32_t swz(uint32_t x) { return x ^ ((x >> 5) & 31u); }
+// XOR swizzle of an element slot x of a tile of 2^logT slots: the low three bits are flipped by
+// the top three.  Row-wise accesses (consecutive slots) stay a permutation of each aligned group
+// of eight; the bit-reversed reads of the first passes (consecutive outputs come from slots that
+// differ in their top bits) land on eight different low-bit patterns, i.e. different banks.
+__device__ __forceinline__ uint32_t swz(uint32_t x, uint32_t logT) {
+  return logT >= 6 ? x ^ ((x >> (logT - 3)) & 7u) : x;
+}
 
 // The tile is element-major: slot x holds the L limbs of one element in L/4 16-byte chunks.
 // With an even chunk count the chunk index is flipped by bit 2 of the slot, so eight
@@ -111,6 +114,7 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
   const uint32_t R = 1u << p.logR;
   const uint32_t G = 1u << p.logG;
   const uint32_t T = R << p.logG;
+  const uint32_t logT = p.logR + p.logG;
   const uint64_t b = tile / p.tiles_per_transform;
   const uint64_t jb = tile - b * p.tiles_per_transform;
   const uint64_t base = b * (uint64_t)L * p.n;
@@ -148,7 +152,7 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
 #pragma unroll
       for (int l = 0; l < L; ++l) v[l] = t[l];
     }
-    tile_store<L>(sm, swz(e), v);  // e = r*G + g
+    tile_store<L>(sm, swz(e, logT), v);  // e = r*G + g
   }
   __syncthreads();
 
@@ -161,7 +165,7 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
       const uint32_t g = bi & (G - 1), u = bi >> p.logG;
       const uint32_t i = u & (h - 1), blk = u >> logh;
       const uint32_t p0 = (blk << (logh + 1)) + i;
-      const uint32_t a0 = swz((p0 << p.logG) + g), a1 = swz(((p0 + h) << p.logG) + g);
+      const uint32_t a0 = swz((p0 << p.logG) + g, logT), a1 = swz(((p0 + h) << p.logG) + g, logT);
       uint32_t x0[L], x1[L];
       tile_load<L>(sm, a0, x0);
       tile_load<L>(sm, a1, x1);
@@ -187,7 +191,7 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
     const uint64_t addr = base + (j - kk) * R + kk + ((uint64_t)sp << p.logNs);
     const uint32_t pr = __brev(sp) >> (32 - p.logR);
     uint32_t v[L];
-    tile_load<L>(sm, swz((pr << p.logG) + g), v);
+    tile_load<L>(sm, swz((pr << p.logG) + g, logT), v);
     if (p.flags & F_LAST) {  // [0, 4q) -> [0, q)
       cond_sub<L>(v, p.k.q2);
       cond_sub<L>(v, p.k.q);
