@@ -292,6 +292,50 @@ def polymul_cyclic(a, b, q: int):
     return ntt_inv([u * v % q for u, v in zip(fa, fb)], q)
 
 
+# ------------------------------------------------------------ negacyclic variant
+# The ring Z_q[x]/(x^n + 1) of lattice schemes: with psi a primitive 2n-th root of unity
+# (psi^2 = w_n), the negacyclic transform evaluates f at the odd powers psi^(2k+1).
+
+def psi_root(q: int, n: int) -> int:
+    """Primitive 2n-th root, psi = g^((q-1)/(2n)) (the root_of_unity reading at 2n), psi^2 = w_n."""
+    return root_of_unity(q, 2 * n)
+
+
+def ntt_fwd_negacyclic(x, q: int):
+    """y(k) = sum_j x(j) psi^(j(2k+1)) = NTT(x(j) psi^j) with w = psi^2."""
+    n = len(x)
+    psi = psi_root(q, n)
+    pre = [x[j] * pow(psi, j, q) % q for j in range(n)]
+    return ntt_radix2(pre, psi * psi % q, q)
+
+
+def ntt_inv_negacyclic(y, q: int):
+    """x(j) = n^-1 psi^-j sum_k y(k) w^(-jk)."""
+    n = len(y)
+    psi = psi_root(q, n)
+    z = ntt_inv(y, q, psi * psi % q)
+    psi_inv = inverse(psi, q)
+    return [z[j] * pow(psi_inv, j, q) % q for j in range(n)]
+
+
+def negacyclic_convolution_naive(a, b, q: int):
+    """c(m) = sum_{i+j=m} a(i) b(j) - sum_{i+j=m+n} a(i) b(j) mod q: the product mod x^n + 1."""
+    n = len(a)
+    c = [0] * n
+    for i in range(n):
+        for j in range(n):
+            if i + j < n:
+                c[i + j] += a[i] * b[j]
+            else:
+                c[i + j - n] -= a[i] * b[j]
+    return [v % q for v in c]
+
+
+def polymul_negacyclic(a, b, q: int):
+    fa, fb = ntt_fwd_negacyclic(a, q), ntt_fwd_negacyclic(b, q)
+    return ntt_inv_negacyclic([u * v % q for u, v in zip(fa, fb)], q)
+
+
 def polymul_naive(a, b):
     """f(x) g(x) = sum_j sum_i a_i b_(j-i) x^j over the integers (Sec. 2.3)."""
     out = [0] * (len(a) + len(b) - 1)

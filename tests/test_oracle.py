@@ -181,6 +181,44 @@ def test_polymul_naive_matches_sympy_poly():
     assert oracle.polymul_naive(a, b) == [int(c) for c in reversed((pa * pb).all_coeffs())]
 
 
+# ------------------------------------------------------------------ negacyclic transforms
+
+@pytest.mark.parametrize("width", [128, 256, 384, 768])
+def test_negacyclic_transform_evaluates_at_odd_powers(width):
+    q = inputs.prime(width).q
+    rng = random.Random(width + 9)
+    for lg in (1, 3, 6):
+        n = 1 << lg
+        x = _rand_vec(rng, n, q)
+        psi = oracle.psi_root(q, n)
+        assert pow(psi, 2 * n, q) == 1 and pow(psi, n, q) == q - 1
+        y = oracle.ntt_fwd_negacyclic(x, q)
+        for k in range(n):
+            assert y[k] == oracle.ntt_eval_at(x, q, 1, pow(psi, 2 * k + 1, q))  # f(psi^(2k+1))
+        assert oracle.ntt_inv_negacyclic(y, q) == x
+
+
+def test_negacyclic_convolution():
+    q = inputs.prime(256).q
+    rng = random.Random(21)
+    for n in (2, 8, 64):
+        a, b = _rand_vec(rng, n, q), _rand_vec(rng, n, q)
+        naive = oracle.negacyclic_convolution_naive(a, b, q)
+        assert oracle.polymul_negacyclic(a, b, q) == naive
+        # the full product over the integers, reduced with x^n = -1
+        full = oracle.polymul_naive(a, b)
+        red = [0] * n
+        for i, v in enumerate(full):
+            red[i % n] += v if i < n else -v
+        assert naive == [v % q for v in red]
+    # x^(n-1) * x = x^n = -1
+    n = 8
+    e = [0] * n
+    e[n - 1] = 1
+    x1 = [0, 1] + [0] * (n - 2)
+    assert oracle.polymul_negacyclic(e, x1, q) == [q - 1] + [0] * (n - 1)
+
+
 # ------------------------------------------------------------------ elementwise ops
 
 @pytest.mark.parametrize("width", [128, 256, 384, 768])
