@@ -133,6 +133,27 @@ moma_status moma_ntt_inv_many(moma_ctx *ctx, size_t n, size_t count, const uint3
 moma_status moma_polymul(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
                          uint32_t *c, void *stream);
 
+/* Negacyclic transforms: the ring Z_q[x]/(x^n + 1) of the FHE schemes named in Sec. 1.
+ * The paper defines only the cyclic transform (Sec. 2.3 Eq. ntt); this library adds the
+ * usual twisted form on top of it.  psi is a primitive 2n-th root of unity with
+ * psi^2 = w_n (the root moma_ntt_fwd uses), so 2n must divide q - 1 (else MOMA_ERR_SIZE).
+ *   forward: out[k] = sum_j in[j] psi^j w_n^(jk) = in evaluated at psi^(2k+1);
+ *   inverse: out[j] = n^-1 psi^-j sum_k in[k] w_n^(-jk), so inverse(forward(x)) = x.
+ * The psi^j factor is applied while the first pass loads its input and n^-1 psi^-j while
+ * the last pass stores its output (one table of n entries per plan, built on first use).
+ * `count` transforms of length n, transform t at in + t*L*n and out + t*L*n, limb-major
+ * as everywhere; out may equal in.  count 0 does nothing. */
+moma_status moma_ntt_fwd_negacyclic(moma_ctx *ctx, size_t n, size_t count, const uint32_t *in,
+                                    uint32_t *out, void *stream);
+moma_status moma_ntt_inv_negacyclic(moma_ctx *ctx, size_t n, size_t count, const uint32_t *in,
+                                    uint32_t *out, void *stream);
+
+/* Negacyclic product c = a * b mod (x^n + 1, q), through the negacyclic transforms, with
+ * the pointwise product fused into the inverse's first pass (as in moma_polymul).
+ * a, b, c: L*n words; c may alias a or b.  2n | q - 1. */
+moma_status moma_polymul_negacyclic(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
+                                    uint32_t *c, void *stream);
+
 /* Same result as moma_ntt_fwd (one transform), but the call allocates no device memory:
  * its intermediate buffers are a fixed 8 MiB array inside the library, held by every GPU
  * that loads it until the process exits.  Meant for callers that may not allocate device
@@ -232,13 +253,17 @@ typedef enum {
  *   max_logr   transforms: largest radix (log2) of one Stockham pass.
  *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment).
  *   cta_threads transforms: threads per CTA (32, 64, 128 or 256).  Each CTA owns one tile;
- *              small CTAs synchronise fewer warps between butterfly stages. */
+ *              small CTAs synchronise fewer warps between butterfly stages.
+ *   tight_regs transforms: 1 = kernels compiled for fewer registers per thread (64 up to 256
+ *              bits, 102 at 384 bits) so that more CTAs of at most 128 threads are resident;
+ *              0 = default. */
 typedef struct {
   int engine;
   int tile_log;
   int max_logr;
   int vec_width;
   int cta_threads;
+  int tight_regs;
 } moma_config;
 
 /* Set / read the schedule used for `op` at size n (transforms: exact n; BLAS: every n).

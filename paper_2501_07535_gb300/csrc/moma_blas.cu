@@ -130,7 +130,7 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
 int vec_max_width(int L) { return L <= 8 ? 4 : (L <= 12 ? 2 : 1); }
 
 moma_config vec_config(const moma_ctx* ctx, int vec_op) {
-  moma_config c = {0, 0, 0, 0, 0};
+  moma_config c = {0, 0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
   if (it != ctx->configs.end()) c = it->second;
   // Karatsuba (engine 3) measured at or above schoolbook at every width for mulmod on GB300

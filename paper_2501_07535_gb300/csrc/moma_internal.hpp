@@ -36,7 +36,9 @@ struct PassDesc {
 struct Plan {
   int logn = 0;
   bool inverse = false;
+  bool negacyclic = false;
   int max_logr = 0;
+  uint32_t* psi = nullptr;  // negacyclic: [n][2L] psi^e (forward) or n^-1 psi^-e (inverse)
   std::vector<PassDesc> passes;
   uint32_t* d_tables = nullptr;  // one allocation holding every table of the plan
   uint32_t scale[kMaxL] = {}, scalep[kMaxL] = {};  // n^-1 and its companion (inverse)
@@ -58,8 +60,8 @@ struct moma_ctx {
   int ntt_ready = 0;  // 0: not yet, 1: ok, -1: modulus not prime
   uint32_t g = 0;     // smallest quadratic non-residue
   int two_adicity = 0;
-  // (logn, inverse, tile_log, max_logr) -> plan
-  std::map<std::tuple<int, int, int, int>, moma::Plan*> plans;
+  // (logn, inverse, tile_log, max_logr, negacyclic) -> plan
+  std::map<std::tuple<int, int, int, int, int>, moma::Plan*> plans;
   // schedule per (op, logn) for transforms, (op, -1) for BLAS; absent = defaults
   std::map<std::pair<int, int>, moma_config> configs;
   int* d_status = nullptr;  // device-side error word
@@ -85,15 +87,16 @@ int max_tile_log(int L);                 // shared-memory limit
 moma_config ntt_config(const moma_ctx* ctx, int op, int logn);  // effective (defaults filled)
 bool ntt_config_valid(int L, int logn, const moma_config& c);
 moma_status ntt_prepare(moma_ctx* ctx);  // primality, generator (takes ctx->lock)
-moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out);
+moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out,
+                     bool negacyclic = false);
 moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in,
                        uint32_t* out, cudaStream_t st);
 moma_status launch_ntt_cfg(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in,
-                           uint32_t* out, const moma_config& cfg, cudaStream_t st);
+                           uint32_t* out, const moma_config& cfg, cudaStream_t st, bool negacyclic = false);
 moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
                            uint32_t* c, cudaStream_t st);
 moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
-                               uint32_t* c, const moma_config& cfg, cudaStream_t st);
+                               uint32_t* c, const moma_config& cfg, cudaStream_t st, bool negacyclic = false);
 void free_plan(Plan* p);
 // Existing plan or null; never builds one (no allocation).
 Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr);

@@ -58,7 +58,7 @@ int max_tile_log(int L) {
 }
 
 moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
-  moma_config c = {0, 0, 0, 0, 0};
+  moma_config c = {0, 0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(op, logn));
   if (it != ctx->configs.end()) c = it->second;
   const NttDefaults d = ntt_defaults(ctx->L);
@@ -78,14 +78,17 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
   if (c.cta_threads != 0 && c.cta_threads != 32 && c.cta_threads != 64 && c.cta_threads != 128 &&
       c.cta_threads != 256)
     return false;
+  if (c.tight_regs != 0 && (c.tight_regs != 1 || c.cta_threads > 128)) return false;
   return true;
 }
 
 // Register cap: 128 per thread up to 384 bits (two 256-thread CTAs per SM at least); the
-// 768-bit kernel needs the full 255.
-template <int L, bool WIDE>
-__global__ void __launch_bounds__(kNttMaxThreads, L <= 12 ? 2 : 1) ntt_pass_kernel(
-    const __grid_constant__ NttPassArgs<L> p) {
+// 768-bit kernel needs the full 255.  TIGHT variants (at most 128 threads per CTA) are compiled
+// for 64 registers up to 256 bits and 102 at 384 bits, without spills, for more resident CTAs.
+template <int L, bool WIDE, bool TIGHT>
+__global__ void __launch_bounds__(TIGHT ? 128 : kNttMaxThreads,
+                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 1)) : (L <= 12 ? 2 : 1))
+    ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ __align__(16) uint32_t sm[];
   ntt_tile<L, WIDE>(p, blockIdx.x, sm);
 }
@@ -98,7 +101,8 @@ struct TwGenArgs {
   // exponent of entry idx: ((idx / D) + C) * (idx % D) * S  (mod n, all < n by construction)
   uint64_t D, C, S;
   uint32_t logn;
-  uint32_t pw[kMaxLogN][L];  // w^(2^b)
+  uint32_t pw[kMaxLogN + 1][L];  // w^(2^b)
+  uint32_t init[L];              // start value of the product (1, or a constant factor)
   uint32_t R0[L];
   uint32_t Q0;
   ModK<L> k;
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(256) twiddle_gen_kernel(const __grid_constant_
     const uint64_t e = ((idx / p.D) + p.C) * (idx % p.D) * p.S & ((1ull << p.logn) - 1);
     uint32_t acc[L];
 #pragma unroll
-    for (int l = 0; l < L; ++l) acc[l] = l == 0 ? 1u : 0u;
+    for (int l = 0; l < L; ++l) acc[l] = p.init[l];
     for (uint32_t bb = 0; bb < p.logn; ++bb) {
       if ((e >> bb) & 1) {
         uint32_t t[L];
@@ -153,7 +157,7 @@ static void fill_modk(const moma_ctx* ctx, ModK<L>& k) {
 
 template <int L>
 static moma_status gen_table(const moma_ctx* ctx, uint32_t* dst, uint64_t count, uint64_t D, uint64_t C,
-                             uint64_t S, int logn, const std::vector<BigU>& pw) {
+                             uint64_t S, int logn, const std::vector<BigU>& pw, const BigU& init) {
   TwGenArgs<L> a;
   a.dst = dst;
   a.count = count;
@@ -161,8 +165,9 @@ static moma_status gen_table(const moma_ctx* ctx, uint32_t* dst, uint64_t count,
   a.C = C;
   a.S = S;
   a.logn = (uint32_t)logn;
-  for (int b = 0; b < kMaxLogN; ++b)
+  for (int b = 0; b <= kMaxLogN; ++b)
     for (int l = 0; l < L; ++l) a.pw[b][l] = b < logn ? pw[b].word(l) : 0u;
+  init.to_words(a.init, L);
   for (int l = 0; l < L; ++l) a.R0[l] = ctx->k.R0[l];
   a.Q0 = ctx->k.Q0;
   fill_modk<L>(ctx, a.k);
@@ -173,12 +178,12 @@ static moma_status gen_table(const moma_ctx* ctx, uint32_t* dst, uint64_t count,
 }
 
 static moma_status gen_table_l(const moma_ctx* ctx, uint32_t* dst, uint64_t count, uint64_t D, uint64_t C,
-                               uint64_t S, int logn, const std::vector<BigU>& pw) {
+                               uint64_t S, int logn, const std::vector<BigU>& pw, const BigU& init = BigU(1)) {
   switch (ctx->L) {
-    case 4: return gen_table<4>(ctx, dst, count, D, C, S, logn, pw);
-    case 8: return gen_table<8>(ctx, dst, count, D, C, S, logn, pw);
-    case 12: return gen_table<12>(ctx, dst, count, D, C, S, logn, pw);
-    case 24: return gen_table<24>(ctx, dst, count, D, C, S, logn, pw);
+    case 4: return gen_table<4>(ctx, dst, count, D, C, S, logn, pw, init);
+    case 8: return gen_table<8>(ctx, dst, count, D, C, S, logn, pw, init);
+    case 12: return gen_table<12>(ctx, dst, count, D, C, S, logn, pw, init);
+    case 24: return gen_table<24>(ctx, dst, count, D, C, S, logn, pw, init);
   }
   return MOMA_ERR_UNSUPPORTED;
 }
@@ -227,11 +232,13 @@ static void split_passes(int logn, int max_logr, std::vector<int>& out) {
   for (int i = 0; i < P; ++i) out.push_back(logn / P + (i < logn % P ? 1 : 0));
 }
 
-static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out) {
+static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, bool nega,
+                              Plan** out) {
   const int L = ctx->L;
   Plan* pl = new Plan();
   pl->logn = logn;
   pl->inverse = inverse;
+  pl->negacyclic = nega;
   pl->tile_log = tile_log;
   pl->max_logr = max_logr;
   const int T = pl->tile_log;
@@ -262,6 +269,7 @@ static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_lo
     pl->passes.push_back(d);
     logNs += lr;
   }
+  if (nega) words += 2ull * L * (1ull << logn);  // psi table, one entry per position
   if (cudaMalloc(&pl->d_tables, words * 4) != cudaSuccess) {
     delete pl;
     return MOMA_ERR_OOM;
@@ -284,11 +292,25 @@ static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_lo
       ptr += 2ull * L * d.tw_count;
     }
   }
+  BigU ninv = sub(ctx->Q, shr(sub(ctx->Q, BigU(1)), logn));  // n^-1 = q - (q-1)/n
   if (inverse) {
-    // n^-1 = q - (q-1)/n
-    BigU ninv = sub(ctx->Q, shr(sub(ctx->Q, BigU(1)), logn));
     ninv.to_words(pl->scale, L);
     companion(ctx, ninv, pl->scalep);
+  }
+  if (nega) {
+    // psi = primitive 2n-th root (psi^2 = w_n); forward table psi^e, inverse n^-1 psi^-e, e < n
+    BigU psi = root_of_unity(ctx, logn + 1);
+    if (inverse) psi = ctx->red->powmod(psi, sub(pow2(logn + 1), BigU(1)));  // psi^(2n-1) = psi^-1
+    std::vector<BigU> ppw;
+    BigU c2 = psi;
+    for (int b = 0; b < logn; ++b) {
+      ppw.push_back(c2);
+      c2 = ctx->red->mulmod(c2, c2);
+    }
+    pl->psi = ptr;
+    moma_status st = gen_table_l(ctx, ptr, 1ull << logn, ~0ull >> 1, 1, 1, logn, ppw, inverse ? ninv : BigU(1));
+    if (st) { free_plan(pl); return st; }
+    ptr += 2ull * L * (1ull << logn);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     free_plan(pl);
@@ -298,27 +320,28 @@ static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_lo
   return MOMA_OK;
 }
 
-moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out) {
+moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out, bool nega) {
   moma_status st = ntt_prepare(ctx);
   if (st) return st;
   if (logn > ctx->two_adicity || logn < 1 || logn > kMaxLogN) return MOMA_ERR_SIZE;
+  if (nega && logn + 1 > ctx->two_adicity) return MOMA_ERR_SIZE;  // needs a 2n-th root
   if (logn <= tile_log) max_logr = 0;  // single pass: the split does not matter
   std::lock_guard<std::mutex> g(ctx->lock);
-  auto key = std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr);
+  auto key = std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr, nega ? 1 : 0);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     *out = it->second;
     return MOMA_OK;
   }
   Plan* pl = nullptr;
-  st = build_plan(ctx, logn, inverse, tile_log, max_logr, &pl);
+  st = build_plan(ctx, logn, inverse, tile_log, max_logr, nega, &pl);
   if (st) return st;
   ctx->plans[key] = pl;
   *out = pl;
   return MOMA_OK;
 }
 
-template <int L, bool WIDE>
+template <int L, bool WIDE, bool TIGHT>
 static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
                             const uint32_t* src2, uint32_t* dst, uint32_t flags, int threads, cudaStream_t st) {
   NttPassArgs<L> a;
@@ -326,7 +349,7 @@ static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, si
   const size_t smem = (size_t)L * 4u << (d.logR + d.logG);
   static bool attr_done = false;
   if (!attr_done) {
-    if (cudaFuncSetAttribute(ntt_pass_kernel<L, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(ntt_pass_kernel<L, WIDE, TIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              L * 4 << max_tile_log(L)) != cudaSuccess)
       return MOMA_ERR_CUDA;
     attr_done = true;
@@ -334,7 +357,7 @@ static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, si
   const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
   if (grid == 0) return MOMA_OK;
   if (grid > 0x7fffffffull) return MOMA_ERR_SIZE;
-  ntt_pass_kernel<L, WIDE><<<(unsigned)grid, threads, smem, st>>>(a);
+  ntt_pass_kernel<L, WIDE, TIGHT><<<(unsigned)grid, threads, smem, st>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -343,16 +366,21 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
                               cudaStream_t st) {
   const bool wide = cfg.engine == 2;
   const int th = cfg.cta_threads;
+  const bool tight = cfg.tight_regs != 0 && th <= 128 && ctx->L <= 12;
+#define MOMA_RUN_PASS(LL)                                                                              \
+  return wide ? (tight ? run_pass<LL, true, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)   \
+                       : run_pass<LL, true, false>(ctx, pl, d, count, src, src2, dst, flags, th, st)) \
+              : (tight ? run_pass<LL, false, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)  \
+                       : run_pass<LL, false, false>(ctx, pl, d, count, src, src2, dst, flags, th, st));
   switch (ctx->L) {
-    case 4: return wide ? run_pass<4, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                        : run_pass<4, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
-    case 8: return wide ? run_pass<8, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                        : run_pass<8, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
-    case 12: return wide ? run_pass<12, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                         : run_pass<12, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
-    case 24: return wide ? run_pass<24, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                         : run_pass<24, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    case 4: MOMA_RUN_PASS(4)
+    case 8: MOMA_RUN_PASS(8)
+    case 12: MOMA_RUN_PASS(12)
+    case 24:
+      return wide ? run_pass<24, true, false>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                  : run_pass<24, false, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   }
+#undef MOMA_RUN_PASS
   return MOMA_ERR_UNSUPPORTED;
 }
 
@@ -375,7 +403,9 @@ static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const u
     uint32_t* dst = (i + 1 == P) ? out : ((i % 2 == 0) ? s1 : s2);
     uint32_t flags = (i + 1 == P) ? F_LAST : 0;
     if (i == 0 && in2) flags |= F_POINTWISE;
-    if (i == 0 && pl->inverse) flags |= F_SCALE;
+    if (i == 0 && pl->inverse && !pl->negacyclic) flags |= F_SCALE;  // negacyclic: n^-1 is in psi
+    if (i == 0 && pl->negacyclic && !pl->inverse) flags |= F_PSI_IN;
+    if (i + 1 == P && pl->negacyclic && pl->inverse) flags |= F_PSI_OUT;
     rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, cfg, st);
     src = dst;
   }
@@ -387,7 +417,7 @@ static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const u
 Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr) {
   if (logn <= tile_log) max_logr = 0;
   std::lock_guard<std::mutex> g(ctx->lock);
-  auto it = ctx->plans.find(std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr));
+  auto it = ctx->plans.find(std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr, 0));
   return it == ctx->plans.end() ? nullptr : it->second;
 }
 
@@ -406,9 +436,9 @@ moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, 
 }
 
 moma_status launch_ntt_cfg(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in, uint32_t* out,
-                           const moma_config& cfg, cudaStream_t st) {
+                           const moma_config& cfg, cudaStream_t st, bool nega) {
   Plan* pl = nullptr;
-  moma_status rc = get_plan(ctx, logn, inverse, cfg.tile_log, cfg.max_logr, &pl);
+  moma_status rc = get_plan(ctx, logn, inverse, cfg.tile_log, cfg.max_logr, &pl, nega);
   if (rc) return rc;
   if (count == 0) return MOMA_OK;
   return run_plan(ctx, pl, count, in, nullptr, out, cfg, st);
@@ -421,11 +451,11 @@ moma_status launch_ntt(moma_ctx* ctx, int logn, size_t count, bool inverse, cons
 }
 
 moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b, uint32_t* c,
-                               const moma_config& cfg, cudaStream_t st) {
+                               const moma_config& cfg, cudaStream_t st, bool nega) {
   Plan *fw = nullptr, *iv = nullptr;
-  moma_status rc = get_plan(ctx, logn, false, cfg.tile_log, cfg.max_logr, &fw);
+  moma_status rc = get_plan(ctx, logn, false, cfg.tile_log, cfg.max_logr, &fw, nega);
   if (rc) return rc;
-  rc = get_plan(ctx, logn, true, cfg.tile_log, cfg.max_logr, &iv);
+  rc = get_plan(ctx, logn, true, cfg.tile_log, cfg.max_logr, &iv, nega);
   if (rc) return rc;
   const size_t words = (size_t)ctx->L << logn;
   uint32_t* fa = nullptr;

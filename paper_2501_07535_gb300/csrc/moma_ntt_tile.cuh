@@ -69,6 +69,7 @@ struct NttPassArgs {
   uint32_t* dst;
   const uint32_t* tw_pass;
   const uint32_t* tw_int;
+  const uint32_t* psi;  // negacyclic pre/post factors, [n][2L] (F_PSI_IN / F_PSI_OUT)
   uint64_t tw_count;
   uint64_t n;
   uint32_t logR, logG, logNs;
@@ -79,8 +80,10 @@ struct NttPassArgs {
 };
 
 // F_PRETW: pre-twiddles (Ns > 1); F_SCALE: multiply by sc at load (n^-1 of the inverse);
-// F_POINTWISE: product with src2 at load (fused polynomial product); F_LAST: canonical store.
-enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4, F_LAST = 8 };
+// F_POINTWISE: product with src2 at load (fused polynomial product); F_LAST: canonical store;
+// F_PSI_IN: multiply input position j by psi[j] at load (negacyclic forward);
+// F_PSI_OUT: multiply output position j by psi[j] at the store (negacyclic inverse).
+enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4, F_LAST = 8, F_PSI_IN = 16, F_PSI_OUT = 32 };
 
 // DIF butterfly on lazy values: a, b in [0, 4q) -> (a + b, (a - b) * w) both in [0, 4q).
 // With MUL false the twiddle is 1.
@@ -144,6 +147,13 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
 #pragma unroll
       for (int l = 0; l < L; ++l) v[l] = t[l];
     }
+    if (p.flags & F_PSI_IN) {
+      uint32_t w[L], wp[L], t[L];
+      twiddle_load<L>(p.psi, j + (uint64_t)r * nR, w, wp);
+      mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l] = t[l];
+    }
     if ((p.flags & F_PRETW) && r != 0 && (j & ns_mask) != 0) {
       const uint64_t ti = (uint64_t)(r - 1) * (ns_mask + 1) + (j & ns_mask);
       uint32_t w[L], wp[L], t[L];
@@ -192,6 +202,13 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
     const uint32_t pr = __brev(sp) >> (32 - p.logR);
     uint32_t v[L];
     tile_load<L>(sm, swz((pr << p.logG) + g, logT), v);
+    if (p.flags & F_PSI_OUT) {  // [0, 4q) -> [0, 3q)
+      uint32_t w[L], wp[L], t[L];
+      twiddle_load<L>(p.psi, addr - base, w, wp);
+      mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
+#pragma unroll
+      for (int l = 0; l < L; ++l) v[l] = t[l];
+    }
     if (p.flags & F_LAST) {  // [0, 4q) -> [0, q)
       cond_sub<L>(v, p.k.q2);
       cond_sub<L>(v, p.k.q);
@@ -211,6 +228,7 @@ inline void fill_pass_args(const moma_ctx* ctx, const Plan* pl, const PassDesc& 
   a.dst = dst;
   a.tw_pass = d.tw_pass;
   a.tw_int = d.tw_int;
+  a.psi = pl->psi;
   a.tw_count = d.tw_count;
   a.n = 1ull << pl->logn;
   a.logR = (uint32_t)d.logR;

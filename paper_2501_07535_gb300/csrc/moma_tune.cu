@@ -97,17 +97,21 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
           const int tl = lth + 3 + t;
           if (tl > max_tile_log(ctx->L)) continue;
           if (lg <= tl) {
-            cands.push_back({engine, tl, tl, 0, th});
+            cands.push_back({engine, tl, tl, 0, th, 0});
+            if (th <= 128) cands.push_back({engine, tl, tl, 0, th, 1});
             continue;
           }
           for (int r = tl - 3; r >= tl - 5; --r)
-            if (r >= 1) cands.push_back({engine, tl, r, 0, th});
+            if (r >= 1) {
+              cands.push_back({engine, tl, r, 0, th, 0});
+              if (th <= 128) cands.push_back({engine, tl, r, 0, th, 1});
+            }
         }
   } else if (is_vec_op(op)) {
     if (n == 0) return MOMA_ERR_SIZE;
     const int engines = op == MOMA_OP_MUL ? 3 : (op == MOMA_OP_AXPY ? 2 : 1);
     for (int engine = 1; engine <= engines; ++engine)
-      for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v, 0});
+      for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v, 0, 0});
   } else {
     return MOMA_ERR_INVALID_ARG;
   }
@@ -132,7 +136,7 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MOMA_ERR_CUDA;
   double best_t = 1e30;
-  moma_config best_c = cands.empty() ? moma_config{0, 0, 0, 0, 0} : cands[0];
+  moma_config best_c = cands.empty() ? moma_config{0, 0, 0, 0, 0, 0} : cands[0];
   moma_status rc = MOMA_OK;
   for (const auto& cfg : cands) {
     rc = run(cfg);  // first use builds the plan (twiddle tables) outside the timing

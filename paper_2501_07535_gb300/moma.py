@@ -59,6 +59,9 @@ _SIGS = {
     "moma_ctx_get_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
     "moma_autotune": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _SZ, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "moma_ntt_fwd_noalloc": (ctypes.c_int, [_P, _SZ, _P, _P, _P]),
+    "moma_ntt_fwd_negacyclic": (ctypes.c_int, [_P, _SZ, _SZ, _P, _P, _P]),
+    "moma_ntt_inv_negacyclic": (ctypes.c_int, [_P, _SZ, _SZ, _P, _P, _P]),
+    "moma_polymul_negacyclic": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
     "moma_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "moma_batch_run": (ctypes.c_int, [_P, _P]),
     "moma_batch_sync_status": (ctypes.c_int, [_P]),
@@ -77,7 +80,7 @@ class moma_job(ctypes.Structure):
 
 class moma_config(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("tile_log", ctypes.c_int), ("max_logr", ctypes.c_int),
-                ("vec_width", ctypes.c_int), ("cta_threads", ctypes.c_int)]
+                ("vec_width", ctypes.c_int), ("cta_threads", ctypes.c_int), ("tight_regs", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -212,6 +215,23 @@ def moma_polymul(ctx, n, a, b, c, stream=None):
     _check(lib().moma_polymul(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)), "moma_polymul")
 
 
+def moma_ntt_fwd_negacyclic(ctx, n, x, y, count=1, stream=None):
+    """Forward transform over Z_q[x]/(x^n + 1): y[k] = x evaluated at psi^(2k+1)."""
+    _check(lib().moma_ntt_fwd_negacyclic(ctx, n, count, _ptr(x), _ptr(y), _stream_handle(stream)),
+           "moma_ntt_fwd_negacyclic")
+
+
+def moma_ntt_inv_negacyclic(ctx, n, x, y, count=1, stream=None):
+    _check(lib().moma_ntt_inv_negacyclic(ctx, n, count, _ptr(x), _ptr(y), _stream_handle(stream)),
+           "moma_ntt_inv_negacyclic")
+
+
+def moma_polymul_negacyclic(ctx, n, a, b, c, stream=None):
+    """c = a * b mod (x^n + 1, q)."""
+    _check(lib().moma_polymul_negacyclic(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)),
+           "moma_polymul_negacyclic")
+
+
 def moma_probe_imad(variant: int, blocks: int, threads: int, iters: int):
     ms = ctypes.c_double()
     cnt = ctypes.c_double()
@@ -224,8 +244,8 @@ def _op(op) -> int:
     return OPS[op] if isinstance(op, str) else int(op)
 
 
-def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0, cta_threads=0):
-    cfg = moma_config(engine, tile_log, max_logr, vec_width, cta_threads)
+def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0, cta_threads=0, tight_regs=0):
+    cfg = moma_config(engine, tile_log, max_logr, vec_width, cta_threads, tight_regs)
     _check(lib().moma_ctx_set_config(ctx, _op(op), n, ctypes.byref(cfg)), "moma_ctx_set_config")
 
 

@@ -1,0 +1,187 @@
+"""Parity of the negacyclic transforms and product (ring Z_q[x]/(x^n + 1)) with the oracle.
+
+Bit-exact (integer path).  The oracle's negacyclic functions are pinned in test_oracle.py
+(evaluation at the odd powers of psi, schoolbook product reduced mod x^n + 1).  Sizes cover
+the single-pass tile and multi-pass splits, in which the psi factor sits in the first pass's
+load (forward) and the last pass's store (inverse); 2^24 is checked on sampled outputs by
+Horner's rule at psi^(2k+1) and by the round trip.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_07535_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+WIDTHS = [128, 256, 384, 768]
+
+
+@pytest.fixture(scope="module")
+def ctxs(gpu):
+    out = {w: gpu.moma_ctx_create(inputs.prime(w).q, w) for w in WIDTHS}
+    yield out
+    for h in out.values():
+        gpu.moma_ctx_destroy(h)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("lg", [1, 2, 5, 10, 11, 13, 15])
+def test_negacyclic_parity(gpu, ctxs, width, lg):
+    if width == 768 and lg > 13:
+        pytest.skip("768-bit oracle transform at 2^15 is slow; 2^13 has the same two-pass split")
+    p = inputs.prime(width)
+    n = 1 << lg
+    x = inputs.residues(p.q, p.L, n, seed=100 + lg)
+    xi = inputs.to_ints(x)
+    dx = gpu.to_device(x)
+    dy, dz = torch.empty_like(dx), torch.empty_like(dx)
+    gpu.moma_ntt_fwd_negacyclic(ctxs[width], n, dx, dy)
+    gpu.moma_ntt_inv_negacyclic(ctxs[width], n, dx, dz)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd_negacyclic(xi, p.q)
+    assert inputs.to_ints(gpu.to_host(dz)) == oracle.ntt_inv_negacyclic(xi, p.q)
+    gpu.moma_ntt_inv_negacyclic(ctxs[width], n, dy, dz)
+    torch.cuda.synchronize()
+    assert torch.equal(dz, dx)
+
+
+@pytest.mark.parametrize("width", [128, 384])
+def test_negacyclic_and_cyclic_plans_coexist(gpu, ctxs, width):
+    """Same size, both transforms interleaved: each keeps its own tables."""
+    p = inputs.prime(width)
+    n = 1 << 12
+    x = inputs.residues(p.q, p.L, n, seed=7)
+    xi = inputs.to_ints(x)
+    dx = gpu.to_device(x)
+    a, b, c = torch.empty_like(dx), torch.empty_like(dx), torch.empty_like(dx)
+    gpu.moma_ntt_fwd(ctxs[width], n, dx, a)
+    gpu.moma_ntt_fwd_negacyclic(ctxs[width], n, dx, b)
+    gpu.moma_ntt_fwd(ctxs[width], n, dx, c)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(a)) == oracle.ntt_fwd(xi, p.q)
+    assert inputs.to_ints(gpu.to_host(b)) == oracle.ntt_fwd_negacyclic(xi, p.q)
+    assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("width", [256, 384])
+def test_negacyclic_many_and_schedules(gpu, width):
+    """count transforms in one call, under schedules with two and three passes."""
+    p = inputs.prime(width)
+    ctx = gpu.moma_ctx_create(p.q, width)
+    try:
+        n, count = 1 << 13, 3
+        x = inputs.residues(p.q, p.L, n * count, seed=55)
+        # transform t occupies columns [t*n, (t+1)*n) of each limb plane in the per-transform
+        # limb-major layout: build that layout explicitly
+        blocks = [np.ascontiguousarray(x[:, t * n:(t + 1) * n]) for t in range(count)]
+        flat = np.concatenate([b.reshape(-1) for b in blocks])
+        dx = gpu.to_device(flat)
+        want_f = [oracle.ntt_fwd_negacyclic(inputs.to_ints(b), p.q) for b in blocks]
+        for tile, rmax, th, tight in ((12, 7, 256, 0), (10, 7, 128, 1), (9, 5, 64, 1), (8, 5, 32, 0)):
+            kw = dict(tile_log=tile, max_logr=rmax, cta_threads=th, tight_regs=tight)
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, **kw)
+            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, **kw)
+            dy, dz = torch.empty_like(dx), torch.empty_like(dx)
+            gpu.moma_ntt_fwd_negacyclic(ctx, n, dx, dy, count=count)
+            gpu.moma_ntt_inv_negacyclic(ctx, n, dy, dz, count=count)
+            torch.cuda.synchronize()
+            got = gpu.to_host(dy).reshape(count, p.L, n)
+            for t in range(count):
+                assert inputs.to_ints(got[t]) == want_f[t], (tile, rmax, th, t)
+            assert torch.equal(dz, dx), (tile, rmax, th)
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("lg", [1, 4, 9, 12])
+def test_polymul_negacyclic_parity(gpu, ctxs, width, lg):
+    p = inputs.prime(width)
+    n = 1 << lg
+    a = inputs.residues(p.q, p.L, n, seed=41)
+    b = inputs.residues(p.q, p.L, n, seed=42)
+    ai, bi = inputs.to_ints(a), inputs.to_ints(b)
+    da, db = gpu.to_device(a), gpu.to_device(b)
+    dc = torch.empty_like(da)
+    gpu.moma_polymul_negacyclic(ctxs[width], n, da, db, dc)
+    torch.cuda.synchronize()
+    got = inputs.to_ints(gpu.to_host(dc))
+    assert got == oracle.polymul_negacyclic(ai, bi, p.q)
+    if lg <= 4:
+        assert got == oracle.negacyclic_convolution_naive(ai, bi, p.q)
+    # in place: c aliases a
+    gpu.moma_polymul_negacyclic(ctxs[width], n, da, db, da)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(da)) == got
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_polymul_negacyclic_wraps_with_sign(gpu, ctxs, width):
+    """x^(n-1) * x = x^n = -1 in Z_q[x]/(x^n + 1); the cyclic product gives +1."""
+    p = inputs.prime(width)
+    n = 1 << 11
+    a = [0] * n
+    b = [0] * n
+    a[n - 1] = 1
+    b[1] = 1
+    da, db = gpu.to_device(inputs.from_ints(a, p.L)), gpu.to_device(inputs.from_ints(b, p.L))
+    dc, dd = torch.empty_like(da), torch.empty_like(da)
+    gpu.moma_polymul_negacyclic(ctxs[width], n, da, db, dc)
+    gpu.moma_polymul(ctxs[width], n, da, db, dd)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dc)) == [p.q - 1] + [0] * (n - 1)
+    assert inputs.to_ints(gpu.to_host(dd)) == [1] + [0] * (n - 1)
+
+
+@pytest.mark.parametrize("width,lg", [(128, 24), (768, 20)])
+def test_negacyclic_large_sampled_and_roundtrip(gpu, ctxs, width, lg):
+    p = inputs.prime(width)
+    n = 1 << lg
+    x = inputs.residues(p.q, p.L, n, seed=124)
+    dx = gpu.to_device(x)
+    dy, dz = torch.empty_like(dx), torch.empty_like(dx)
+    gpu.moma_ntt_fwd_negacyclic(ctxs[width], n, dx, dy)
+    gpu.moma_ntt_inv_negacyclic(ctxs[width], n, dy, dz)
+    torch.cuda.synchronize()
+    assert torch.equal(dz, dx)
+    psi = oracle.psi_root(p.q, n)
+    xi = inputs.to_ints(x)
+    ks = [0, n - 1, int(np.random.Generator(np.random.PCG64(width)).integers(1, n - 1))]
+    got = inputs.to_ints(gpu.to_host(dy[:, torch.tensor(ks, device="cuda")]))
+    assert got == [oracle.ntt_eval_at(xi, p.q, 2 * k + 1, psi) for k in ks]
+
+
+def _prime_with_two_adicity(bits: int, s: int) -> int:
+    """Smallest q = k 2^s + 1 with k odd and q of exactly `bits` bits that is prime."""
+    k = (1 << (bits - 1 - s)) + 1
+    while True:
+        q = (k << s) + 1
+        if oracle.is_probable_prime(q):
+            return q
+        k += 2
+
+
+def test_negacyclic_needs_2n_dividing_q_minus_1(gpu):
+    s = 12
+    q = _prime_with_two_adicity(124, s)
+    assert oracle.two_adicity(q) == s
+    ctx = gpu.moma_ctx_create(q, 128)
+    try:
+        n = 1 << s
+        x = inputs.residues(q, 4, n, seed=3)
+        dx = gpu.to_device(x)
+        dy = torch.empty_like(dx)
+        gpu.moma_ntt_fwd(ctx, n, dx, dy)  # the cyclic transform of this size exists
+        torch.cuda.synchronize()
+        assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), q)
+        for call in (lambda: gpu.moma_ntt_fwd_negacyclic(ctx, n, dx, dy),
+                     lambda: gpu.moma_ntt_inv_negacyclic(ctx, n, dx, dy),
+                     lambda: gpu.moma_polymul_negacyclic(ctx, n, dx, dx, dy)):
+            with pytest.raises(gpu.MomaError) as e:
+                call()
+            assert gpu.STATUS[e.value.code] == "MOMA_ERR_SIZE"
+        gpu.moma_ntt_fwd_negacyclic(ctx, n // 2, dx[:, : n // 2].contiguous(), dy[:, : n // 2].contiguous())
+        torch.cuda.synchronize()
+    finally:
+        gpu.moma_ctx_destroy(ctx)

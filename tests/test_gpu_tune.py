@@ -18,15 +18,18 @@ def test_ntt_every_engine_and_split(gpu, width, engine):
     p = inputs.prime(width)
     ctx = gpu.moma_ctx_create(p.q, width)
     try:
-        for lg, tile, rmax, th in ((10, 11, 6, 256), (13, 10, 5, 256), (13, 11, 8, 128), (15, 12, 7, 256),
-                                   (13, 8, 5, 32), (16, 9, 6, 64), (10, 10, 7, 128), (7, 8, 5, 32)):
+        for lg, tile, rmax, th, tight in ((10, 11, 6, 256, 0), (13, 10, 5, 256, 0), (13, 11, 8, 128, 0),
+                                          (15, 12, 7, 256, 0), (13, 8, 5, 32, 1), (16, 9, 6, 64, 0),
+                                          (10, 10, 7, 128, 1), (7, 8, 5, 32, 0), (14, 9, 5, 128, 1)):
             if tile > 12 and p.L == 12:
                 continue
             n = 1 << lg
-            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, engine=engine, tile_log=tile, max_logr=rmax, cta_threads=th)
-            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, engine=engine, tile_log=tile, max_logr=rmax, cta_threads=th)
+            kw = dict(engine=engine, tile_log=tile, max_logr=rmax, cta_threads=th, tight_regs=tight)
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, **kw)
+            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, **kw)
             cfg = gpu.moma_ctx_get_config(ctx, "ntt_fwd", n)
-            assert (cfg["engine"], cfg["tile_log"], cfg["max_logr"], cfg["cta_threads"]) == (engine, tile, rmax, th)
+            assert (cfg["engine"], cfg["tile_log"], cfg["max_logr"], cfg["cta_threads"], cfg["tight_regs"]) == \
+                (engine, tile, rmax, th, tight)
             x = inputs.residues(p.q, p.L, n, seed=lg + engine)
             dx = gpu.to_device(x)
             dy = torch.empty_like(dx)
@@ -100,5 +103,7 @@ def test_config_rejects_invalid(gpu):
             gpu.moma_ctx_set_config(ctx, "mul", 1 << 10, vec_width=3)
         with pytest.raises(gpu.MomaError):
             gpu.moma_ctx_set_config(ctx, 99, 1 << 10)
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", 1 << 10, cta_threads=256, tight_regs=1)
     finally:
         gpu.moma_ctx_destroy(ctx)
