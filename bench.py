@@ -40,7 +40,12 @@ L = WIDTH // 32
 # from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule
 # and kernel version (None otherwise).
 NTT_PASS_TRAFFIC_BYTES = None
-NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 1, "tile_log": 10, "max_logr": 5, "vec_width": 0, "cta_threads": 128}
+NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 1, "tile_log": 10, "max_logr": 5, "cta_threads": 128, "tight_regs": 0}
+
+# Integer-multiply peak from the unit counts: the multiply pipe (fmaheavy) of each of the 4 SM
+# sub-partitions takes one whole 32x32->64 product (mad.wide) per 4 cycles per warp, i.e. 8 lane
+# products per clock, 32 per SM per clock (moma_probe_imad measures the 4 cycles).
+PRODUCTS_PER_CLK_PER_SM = 32
 
 
 def word_products_per_mulmod(L):
@@ -219,7 +224,9 @@ def run_ours(args):
     for variant, per_op in ((5, 1.0), (0, 0.5)):
         pms, pops = moma.moma_probe_imad(variant, sms * 8, 256, 2000)
         probe[variant] = pops * per_op / (pms * 1e-3)
-    prod_peak = max(probe.values())  # word products / s
+    probe_peak = max(probe.values())  # word products / s, fastest form measured in this run
+    sm_max_mhz = _measured_peaks().get("sm_max_mhz") or 2070.0
+    prod_peak = sms * PRODUCTS_PER_CLK_PER_SM * sm_max_mhz * 1e6  # unit-count peak at the max SM clock
 
     # ---- NTT region
     def ntt_step():
@@ -329,9 +336,12 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": round(ntt_achieved, 3), "peak": round(peak_t, 3),
                      "unit": "T word-products/s", "frac": round(ntt_achieved / peak_t, 4),
-                     "traffic": NTT_PASS_TRAFFIC_BYTES if ntt_cfg == NTT_PASS_TRAFFIC_SCHEDULE else None,
-                     "peak_source": "measured in this run by moma_probe_imad: fastest 32x32->64 product form "
-                                    "(mad.wide) on all SMs",
+                     "traffic": NTT_PASS_TRAFFIC_BYTES if all(ntt_cfg.get(k) == v for k, v in
+                                                              NTT_PASS_TRAFFIC_SCHEDULE.items()) else None,
+                     "peak_source": f"{sms} SMs x {PRODUCTS_PER_CLK_PER_SM} whole 32x32->64 products (mad.wide) "
+                                    f"per clock per SM x {sm_max_mhz:.0f} MHz max SM clock",
+                     "peak_probe": round(probe_peak / 1e12, 3),
+                     "frac_of_probe": round(ntt_achieved / (probe_peak / 1e12), 4),
                      "algorithmic": f"(n/2)log2(n) mulmods x (2L^2+L) = {word_products_per_mulmod(L)} word "
                                     f"products per mulmod, {NTT_BATCH} transforms per step"},
         "mulmod": {"value": round(gelem, 3), "unit": "Gelem/s", "ms_per_step": round(mul_ms / args.steps, 4),

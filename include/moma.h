@@ -15,8 +15,8 @@
  * Widths.  bits in {128, 256, 384, 768}; L = bits/32 limbs of 32 bits.  The modulus
  *   q must be odd and have exactly bits-4 bits (Sec. 5.2: a (k-4)-bit modulus for a
  *   k-bit container, which the Barrett constants of Sec. 3.1 need); otherwise
- *   MOMA_ERR_MODULUS.  Every width is supported by every call, except transform jobs inside
- *   batches (128 to 384 bits) and moma_ntt_fwd_noalloc (128 to 384 bits).
+ *   MOMA_ERR_MODULUS.  Every width is supported by every call, except moma_ntt_fwd_noalloc
+ *   (128 to 384 bits).
  * Layout.  A vector of n residues is limb-major: uint32 v[L][n], limb 0 the least
  *   significant word of each residue (the paper writes words most significant first;
  *   that is notation only).  Plane j of element i is at v[j*n + i].
@@ -179,9 +179,10 @@ moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, ui
 /* One job of a batch.  op: MOMA_OP_NTT_FWD / NTT_INV (a -> out), MOMA_OP_POLYMUL
  * (out = a * b mod (x^n - 1, q)), MOMA_OP_ADD / SUB / MUL (out = a op b), MOMA_OP_AXPY
  * (out = alpha * a + b, alpha a HOST array of L limbs).  Device vectors follow the
- * conventions above; each job uses its own context (any widths and moduli may be mixed;
- * transforms at 128 to 384 bits, vector ops at every width; a 768-bit transform job gives
- * MOMA_ERR_UNSUPPORTED, use the per-call transforms for those). */
+ * conventions above; each job uses its own context (any widths and moduli may be mixed).
+ * Transforms at 128 to 384 bits and vector ops at every width are tiles of the persistent
+ * launch; 768-bit transform jobs run as per-pass launches right after it, on the same stream
+ * (and in the same CUDA graph). */
 typedef struct {
   int op;
   moma_ctx *ctx;

@@ -15,7 +15,9 @@
 //
 // Widths are mixed inside one launch: the CTA dispatches on the tile's limb count.  Products
 // use whole mad.wide rows up to 256 bits and carry chains at 384 bits (the faster form of each
-// width on GB300); results are identical either way.
+// width on GB300); results are identical either way.  768-bit transforms are not tiles of the
+// persistent kernel (their registers would cut the occupancy of every other tile): they run as
+// per-pass launches right after it, on the same stream and inside the same CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -155,8 +157,24 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __re
 
 using namespace moma;
 
+// A 768-bit transform job of a batch, run with the per-call pass kernels after the
+// persistent launch (intermediates in the batch's scratch: [s1 | s2 | fa | fb]).
+struct BatchDeferred {
+  int op = 0;
+  moma_ctx* ctx = nullptr;
+  const moma::Plan* fwd = nullptr;
+  const moma::Plan* inv = nullptr;
+  const uint32_t* a = nullptr;
+  const uint32_t* b = nullptr;
+  uint32_t* out = nullptr;
+  uint32_t* scratch = nullptr;
+  size_t w = 0;
+  moma_config cfg = {};
+};
+
 struct moma_batch {
   int device = 0;
+  std::vector<BatchDeferred> deferred;
   int runs = 0;
   std::vector<Seg> segs;
   uint32_t total = 0;
@@ -327,12 +345,10 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     }
     const int lg = log2_n(jb.n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-    // 768-bit transform tiles would raise the persistent kernel's register budget (and cut
-    // the occupancy of every other tile); 768-bit transforms run through the per-call API
-    if (ctx->L > 12) return MOMA_ERR_UNSUPPORTED;
     moma_config cfg = ntt_config(ctx, jb.op, lg);
-    const int tl = std::min(cfg.tile_log, kBatchTileLog);
-    const int rmax = std::min(cfg.max_logr, tl);
+    // 768-bit transforms keep their per-call schedule (they run as per-pass launches)
+    const int tl = ctx->L > 12 ? cfg.tile_log : std::min(cfg.tile_log, kBatchTileLog);
+    const int rmax = ctx->L > 12 ? cfg.max_logr : std::min(cfg.max_logr, tl);
     Plan* pl = nullptr;
     moma_status rc;
     if (jb.op != MOMA_OP_NTT_INV) {
@@ -375,7 +391,20 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     const uint32_t no_id[2] = {0, 0}, no_cnt[2] = {0, 0};
     uint32_t* base = b->d_scratch + scratch_off[j];
     const size_t w = (size_t)ctx->L * jb.n;
-    if (jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV) {
+    if (jb.op <= MOMA_OP_POLYMUL && ctx->L > 12) {
+      BatchDeferred d;
+      d.op = jb.op;
+      d.ctx = ctx;
+      d.fwd = fwd[j];
+      d.inv = inv[j];
+      d.a = jb.a;
+      d.b = jb.b;
+      d.out = jb.out;
+      d.scratch = base;
+      d.w = w;
+      d.cfg = ntt_config(ctx, jb.op, log2_n(jb.n));
+      b->deferred.push_back(d);
+    } else if (jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV) {
       const Plan* pl = jb.op == MOMA_OP_NTT_FWD ? fwd[j] : inv[j];
       uint32_t tiles = 0;
       rc = add_transform(ctx, pl, j, 0, 0, counter++, jb.a, nullptr, jb.out, base, base + w, no_id, no_cnt, ab, pend,
@@ -422,7 +451,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     return std::make_tuple(x.level, x.job, x.sub) < std::make_tuple(y.level, y.job, y.sub);
   });
   if (cudaMallocAsync(&b->d_args, std::max<size_t>(ab.bytes.size(), 16), ss) != cudaSuccess ||
-      cudaMallocAsync(&b->d_segs, pend.size() * sizeof(Seg), ss) != cudaSuccess ||
+      cudaMallocAsync(&b->d_segs, std::max<size_t>(pend.size(), 1) * sizeof(Seg), ss) != cudaSuccess ||
       cudaMallocAsync(&b->d_ctr, (1 + counter) * sizeof(uint32_t), ss) != cudaSuccess ||
       cudaMallocAsync(&b->d_status, sizeof(int), ss) != cudaSuccess) {
     moma_batch_destroy(b);
@@ -451,7 +480,8 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
   // shared memory: the largest transform tile of the batch
   size_t smem = 0;
   for (int j = 0; j < njobs; ++j)
-    if (jobs[j].op <= MOMA_OP_POLYMUL) smem = std::max(smem, (size_t)jobs[j].ctx->L * 4u << kBatchTileLog);
+    if (jobs[j].op <= MOMA_OP_POLYMUL && jobs[j].ctx->L <= 12)
+      smem = std::max(smem, (size_t)jobs[j].ctx->L * 4u << kBatchTileLog);
   b->smem = smem;
   if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(12 * 4 << kBatchTileLog)) !=
       cudaSuccess) {
@@ -470,10 +500,31 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
 }
 
 static moma_status batch_launch(moma_batch* b, cudaStream_t st) {
-  if (cudaMemsetAsync(b->d_ctr, 0, (1 + b->ncounters) * sizeof(uint32_t), st) != cudaSuccess) return MOMA_ERR_CUDA;
-  batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_segs, (uint32_t)b->segs.size(), b->total, b->d_ctr,
-                                                        b->d_status, b->wait_polls);
-  return cuda_status(cudaGetLastError());
+  if (b->total > 0) {
+    if (cudaMemsetAsync(b->d_ctr, 0, (1 + b->ncounters) * sizeof(uint32_t), st) != cudaSuccess) return MOMA_ERR_CUDA;
+    batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_segs, (uint32_t)b->segs.size(), b->total, b->d_ctr,
+                                                          b->d_status, b->wait_polls);
+    const moma_status rc = cuda_status(cudaGetLastError());
+    if (rc) return rc;
+  }
+  for (const BatchDeferred& d : b->deferred) {
+    uint32_t* s1 = d.scratch;
+    uint32_t* s2 = d.scratch + d.w;
+    moma_status rc;
+    if (d.op == MOMA_OP_NTT_FWD) {
+      rc = run_plan_buffers(d.ctx, d.fwd, 1, d.a, nullptr, d.out, d.cfg, s1, s2, st);
+    } else if (d.op == MOMA_OP_NTT_INV) {
+      rc = run_plan_buffers(d.ctx, d.inv, 1, d.a, nullptr, d.out, d.cfg, s1, s2, st);
+    } else {
+      uint32_t* fa = d.scratch + 2 * d.w;
+      uint32_t* fb = d.scratch + 3 * d.w;
+      rc = run_plan_buffers(d.ctx, d.fwd, 1, d.a, nullptr, fa, d.cfg, s1, s2, st);
+      if (!rc) rc = run_plan_buffers(d.ctx, d.fwd, 1, d.b, nullptr, fb, d.cfg, s1, s2, st);
+      if (!rc) rc = run_plan_buffers(d.ctx, d.inv, 1, fa, fb, d.out, d.cfg, s1, s2, st);
+    }
+    if (rc) return rc;
+  }
+  return MOMA_OK;
 }
 
 extern "C" moma_status moma_batch_run(moma_batch* b, void* stream) {

@@ -98,6 +98,10 @@ moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uin
 moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
                                uint32_t* c, const moma_config& cfg, cudaStream_t st, bool negacyclic = false);
 void free_plan(Plan* p);
+// Every pass of a plan with caller-provided intermediate buffers (s1, s2: count*L*n words each;
+// s1 may be null for a one-pass plan, s2 for plans of up to two passes).
+moma_status run_plan_buffers(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
+                             uint32_t* out, const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st);
 // Existing plan or null; never builds one (no allocation).
 Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr);
 // All passes of an existing single-transform plan with caller-provided scratch

@@ -457,6 +457,12 @@ MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uin
 //   s = floor(a*wp / 2^(32L)) (truncated, exact or one less);  r = a*w - s*q mod 2^(32L).
 // For any a < 2^(32L): a*w/q - s < 3, so r lies in [0, 3q), which fits the container.
 // Used for twiddle factors (tables carry the companion) and for the axpy scalar.
+#ifndef MOMA_FIXED_HI_WIDE
+#define MOMA_FIXED_HI_WIDE 1
+#endif
+#ifndef MOMA_FIXED_LO_WIDE
+#define MOMA_FIXED_LO_WIDE 1
+#endif
 template <int L, bool WIDE = false>
 MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
                                 const uint32_t (&wp)[L], const ModK<L>& k) {
@@ -464,9 +470,15 @@ MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const 
 #pragma unroll
   for (int i = 0; i < L; ++i) r[i] = 0u;
   if constexpr (WIDE) {
-    mul_hi_trunc_w<L>(s, a, wp);
-    mul_lo_acc_w<L>(r, a, w);
-    mul_lo_acc_w<L>(r, s, k.nq);
+    if constexpr (MOMA_FIXED_HI_WIDE) mul_hi_trunc_w<L>(s, a, wp);
+    else mul_hi_trunc<L>(s, a, wp);
+    if constexpr (MOMA_FIXED_LO_WIDE) {
+      mul_lo_acc_w<L>(r, a, w);
+      mul_lo_acc_w<L>(r, s, k.nq);
+    } else {
+      mul_lo_acc<L>(r, a, w);
+      mul_lo_acc<L>(r, s, k.nq);
+    }
   } else {
     mul_hi_trunc<L>(s, a, wp);
     mul_lo_acc<L>(r, a, w);

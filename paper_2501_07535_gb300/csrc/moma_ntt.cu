@@ -85,9 +85,12 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
 // Register cap: 128 per thread up to 384 bits (two 256-thread CTAs per SM at least); the
 // 768-bit kernel needs the full 255.  TIGHT variants (at most 128 threads per CTA) are compiled
 // for 64 registers up to 256 bits and 102 at 384 bits, without spills, for more resident CTAs.
+#ifndef MOMA_NTT_MINB
+#define MOMA_NTT_MINB 3
+#endif
 template <int L, bool WIDE, bool TIGHT>
 __global__ void __launch_bounds__(TIGHT ? 128 : kNttMaxThreads,
-                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 1)) : (L <= 12 ? 2 : 1))
+                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 1)) : (L <= 12 ? MOMA_NTT_MINB : 1))
     ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ __align__(16) uint32_t sm[];
   ntt_tile<L, WIDE>(p, blockIdx.x, sm);
@@ -384,19 +387,13 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
   return MOMA_ERR_UNSUPPORTED;
 }
 
-// Run every pass of a plan: in -> [scratch1 -> scratch2 -> ...] -> out.  The first pass can
-// fuse a pointwise product with src2 (polymul) and, for the inverse, the n^-1 scaling.
-static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
-                            uint32_t* out, const moma_config& cfg, cudaStream_t st) {
+// Run every pass of a plan: in -> [s1 -> s2 -> s1 ...] -> out, with caller-provided
+// intermediate buffers (each count*L*n words; s1 unused for one pass, s2 for up to two).  The
+// first pass can fuse a pointwise product with in2 (polymul) and, for the inverse, the n^-1
+// scaling; negacyclic plans apply psi at the first load or the last store.
+moma_status run_plan_buffers(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
+                             uint32_t* out, const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st) {
   const size_t P = pl->passes.size();
-  const size_t words = (size_t)ctx->L * ((size_t)1 << pl->logn) * count;
-  uint32_t* s1 = nullptr;
-  uint32_t* s2 = nullptr;
-  if (P >= 2 && cudaMallocAsync(&s1, words * 4, st) != cudaSuccess) return MOMA_ERR_OOM;
-  if (P >= 3 && cudaMallocAsync(&s2, words * 4, st) != cudaSuccess) {
-    cudaFreeAsync(s1, st);
-    return MOMA_ERR_OOM;
-  }
   moma_status rc = MOMA_OK;
   const uint32_t* src = in;
   for (size_t i = 0; i < P && rc == MOMA_OK; ++i) {
@@ -409,6 +406,22 @@ static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const u
     rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, cfg, st);
     src = dst;
   }
+  return rc;
+}
+
+// run_plan_buffers with intermediate buffers from the stream-ordered pool.
+static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
+                            uint32_t* out, const moma_config& cfg, cudaStream_t st) {
+  const size_t P = pl->passes.size();
+  const size_t words = (size_t)ctx->L * ((size_t)1 << pl->logn) * count;
+  uint32_t* s1 = nullptr;
+  uint32_t* s2 = nullptr;
+  if (P >= 2 && cudaMallocAsync(&s1, words * 4, st) != cudaSuccess) return MOMA_ERR_OOM;
+  if (P >= 3 && cudaMallocAsync(&s2, words * 4, st) != cudaSuccess) {
+    cudaFreeAsync(s1, st);
+    return MOMA_ERR_OOM;
+  }
+  const moma_status rc = run_plan_buffers(ctx, pl, count, in, in2, out, cfg, s1, s2, st);
   if (s1) cudaFreeAsync(s1, st);
   if (s2) cudaFreeAsync(s2, st);
   return rc;

@@ -167,12 +167,26 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
   __syncthreads();
 
   // ---- R-point transforms: logR radix-2 DIF stages, in place in the tile
+#ifndef MOMA_STAGE_BALANCE
+#define MOMA_STAGE_BALANCE 1
+#endif
+#ifndef MOMA_STAGE_UNROLL
+#define MOMA_STAGE_UNROLL 1
+#endif
+  constexpr int kStageUnroll = MOMA_STAGE_UNROLL;
+  const uint32_t logNT = 31u - (uint32_t)__clz(blockDim.x);
+  const uint32_t logW = (MOMA_STAGE_BALANCE && logNT > p.logG) ? logNT - p.logG : 0u;
 #pragma unroll 1
   for (uint32_t s = 0; s < p.logR; ++s) {
     const uint32_t logh = p.logR - s - 1;
     const uint32_t h = 1u << logh;
+#pragma unroll kStageUnroll
     for (uint32_t bi = threadIdx.x; bi < (T >> 1); bi += blockDim.x) {
-      const uint32_t g = bi & (G - 1), u = bi >> p.logG;
+      // butterfly row u of group g; the W = NT/G rows one pass of the CTA takes are rotated by
+      // the pass index, so that every warp gets its share of the unit-twiddle (i = 0) rows
+      const uint32_t g = bi & (G - 1), u0 = bi >> p.logG;
+      const uint32_t uh = u0 >> logW, wm = (1u << logW) - 1;
+      const uint32_t u = (uh << logW) | ((u0 + uh) & wm);
       const uint32_t i = u & (h - 1), blk = u >> logh;
       const uint32_t p0 = (blk << (logh + 1)) + i;
       const uint32_t a0 = swz((p0 << p.logG) + g, logT), a1 = swz(((p0 + h) << p.logG) + g, logT);

@@ -164,7 +164,10 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   if (rc) return rc;
   rc = moma_ctx_set_config(ctx, op, n, &best_c);
   if (rc) return rc;
-  if (best) *best = best_c;
+  if (best) {  // the effective schedule, defaults filled in (as moma_ctx_get_config reports it)
+    std::lock_guard<std::mutex> g(ctx->lock);
+    *best = lg >= 0 ? ntt_config(ctx, op, lg) : vec_config(ctx, op - MOMA_OP_ADD);
+  }
   if (best_us) *best_us = best_t;
   return MOMA_OK;
 }

@@ -241,17 +241,9 @@ class GpuExecutor:
 
 
 def served_jobs(n_jobs=10000, seed=0, rate_per_s=1000.0):
-    """The served stream: transforms at 256/384 bits (768-bit transforms are not built in this
-    version, so 768-bit requests are vector ops), vectors at 256/384/768 bits."""
-    arrivals, jobs = inputs.served_stream(n_jobs=n_jobs, seed=seed, rate_per_s=rate_per_s)
-    out = []
-    for j in jobs:
-        if j.width == 768 and j.op in ("ntt_fwd", "ntt_inv"):
-            lg = int(np.log2(j.n)) + 2  # same seed-derived size range shifted into the vector range
-            j = inputs.Job(op="mul" if j.op == "ntt_fwd" else "axpy", width=768, n=1 << min(max(lg, 16), 24),
-                           seed=j.seed, prime_seed=j.prime_seed)
-        out.append(j)
-    return arrivals, out
+    """The served stream: transforms (2^12..2^22) and mulmod/axpy vectors (2^16..2^24) at
+    256/384/768 bits, Poisson arrivals."""
+    return inputs.served_stream(n_jobs=n_jobs, seed=seed, rate_per_s=rate_per_s)
 
 
 def serve(arrivals, jobs, contexts, slots=4, budget_bytes=BUDGET_BYTES, max_batch_jobs=64, executor=None):

@@ -32,7 +32,9 @@ def _mixed_jobs():
     jobs = inputs.uneven_batch(n_jobs=24, seed=5, log_n_range=(1, 13), widths=(128, 256, 384))
     jobs += [inputs.Job(op=op, width=w, n=n, seed=3000 + i)
              for i, (op, w, n) in enumerate([("add", 768, 5000), ("sub", 128, 4099), ("mul", 256, 2048),
-                                             ("axpy", 384, 3), ("mul", 768, 777), ("axpy", 128, 10000)])]
+                                             ("axpy", 384, 3), ("mul", 768, 777), ("axpy", 128, 10000),
+                                             ("ntt_fwd", 768, 1 << 10), ("ntt_inv", 768, 1 << 12),
+                                             ("polymul", 768, 1 << 9), ("ntt_fwd", 768, 2)])]
     return jobs
 
 
@@ -66,6 +68,31 @@ def test_batch_matches_oracle_and_plain(gpu):
         assert js.status() == 0
         for i in range(len(js.jobs)):
             assert (moma.to_host(js.out[i]) == got[i]).all(), i
+    finally:
+        js.close()
+        js.ctx.close()
+
+
+def test_batch_of_768bit_transforms_only(gpu):
+    """768-bit transforms run as per-pass launches after the persistent launch; a batch with
+    nothing else skips the persistent launch.  Direct run, then graph capture and replay."""
+    jobs = [inputs.Job(op=op, width=768, n=n, seed=4000 + i)
+            for i, (op, n) in enumerate([("ntt_fwd", 1 << 11), ("polymul", 1 << 8), ("ntt_inv", 1 << 9)])]
+    js = batch.JobSet(jobs)
+    try:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                for o in js.out:
+                    o.zero_()
+                js.run_batched(s)
+        s.synchronize()
+        assert js.status() == 0
+        for i, j in enumerate(js.jobs):
+            q = inputs.prime(j.width, j.prime_seed).q
+            a = inputs.to_ints(js.host_a[i])
+            b = inputs.to_ints(js.host_b[i]) if js.host_b[i] is not None else None
+            assert inputs.to_ints(moma.to_host(js.out[i])) == _oracle(j, a, b, None, q), (i, j)
     finally:
         js.close()
         js.ctx.close()

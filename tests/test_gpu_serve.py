@@ -11,8 +11,7 @@ pytestmark = pytest.mark.gpu
 def test_served_results_equal_alone(gpu):
     arrivals, jobs = inputs.served_stream(n_jobs=160, seed=3, rate_per_s=20000.0, ntt_log_range=(6, 12),
                                           vec_log_range=(8, 14))
-    jobs = [inputs.Job(op=("mul" if (j.width == 768 and j.op.startswith("ntt")) else j.op), width=j.width,
-                       n=j.n, seed=j.seed, prime_seed=j.prime_seed) for j in jobs]
+    assert any(j.width == 768 and j.op.startswith("ntt") for j in jobs)
     ctxs = batch.Contexts()
     ex = serve.GpuExecutor(ctxs, slots=4, keep_outputs=True, master_log=12)
     try:

@@ -74,8 +74,9 @@ def test_served_stream_shape():
     assert len(jobs) == 2000 and arrivals == sorted(arrivals)
     assert abs(arrivals[-1] / 2000 - 1e-3) < 2e-4  # Poisson rate
     assert {j.width for j in jobs} == {256, 384, 768}
+    assert {j.width for j in jobs if j.op.startswith("ntt")} == {256, 384, 768}
     for j in jobs:
         if j.op in ("ntt_fwd", "ntt_inv"):
-            assert j.width in (256, 384) and 1 << 12 <= j.n <= 1 << 22
+            assert j.width in (256, 384, 768) and 1 << 12 <= j.n <= 1 << 22
         else:
             assert j.op in ("mul", "axpy") and 1 << 16 <= j.n <= 1 << 24
