@@ -343,3 +343,52 @@ def polymul_naive(a, b):
         for j, bj in enumerate(b):
             out[i + j] += ai * bj
     return out
+
+
+# ------------------------------------------------------------ full-width moduli, Montgomery
+# Sec. 5.2 names Montgomery reduction for moduli that fill their container (B = W bits), where
+# the Barrett constants of Sec. 3.1 no longer fit.  R = 2^W.  Montgomery's REDC (T -> T R^-1 mod q
+# for T < q R) is taken word by word, 32 bits at a time, in the order of the usual
+# operand-scanning form: for each of the L words, m = (T mod 2^32) * q' mod 2^32 with
+# q' = -q^-1 mod 2^32, T = (T + m q) / 2^32; one final conditional subtraction.
+
+def gen_prime_full(width: int, seed: int) -> int:
+    """NTT-friendly prime q = c*2^32 + 1 of exactly W bits (a full-width modulus).
+
+    c is drawn from random.Random("moma-full:<W>:<seed>") uniformly in [2^(W-33), 2^(W-32)).
+    """
+    rng = random.Random(f"moma-full:{width}:{seed}")
+    while True:
+        c = rng.randrange(1 << (width - 33), 1 << (width - 32))
+        q = (c << 32) + 1
+        if is_probable_prime(q, rng):
+            return q
+
+
+def montgomery_qinv_word(q: int) -> int:
+    """q' = -q^-1 mod 2^32 (q odd)."""
+    return (-pow(q, -1, 1 << 32)) % (1 << 32)
+
+
+def montgomery_redc_words(T: int, q: int, width: int, final: bool = True) -> int:
+    """T R^-1 mod q for 0 <= T < q R, R = 2^W, one 32-bit word of T per step.
+
+    Without the final subtraction the result lies in [0, 2q)."""
+    qi = montgomery_qinv_word(q)
+    for _ in range(width // 32):
+        m = (T & 0xFFFFFFFF) * qi & 0xFFFFFFFF
+        T = (T + m * q) >> 32
+    if final and T >= q:
+        T -= q
+    return T
+
+
+def montgomery_mul(a: int, b: int, q: int, width: int) -> int:
+    """a b R^-1 mod q for canonical a, b (REDC of the full product)."""
+    return montgomery_redc_words(a * b, q, width)
+
+
+def mulmod_via_montgomery(a: int, b: int, q: int, width: int) -> int:
+    """a b mod q as two Montgomery products: REDC(REDC(a b) (R^2 mod q))."""
+    r2 = (1 << (2 * width)) % q
+    return montgomery_mul(montgomery_mul(a, b, q, width), r2, q, width)

@@ -88,7 +88,7 @@ class Prime:
     width: int      # container width W (bits)
     seed: int
     q: int
-    bits: int       # bit length of q, = W - 4
+    bits: int       # bit length of q: W - 4 (Barrett contexts) or W (full-width contexts)
     two_adicity: int
 
     @property
@@ -110,6 +110,22 @@ def load_primes(path: str = PRIMES_JSON) -> dict[tuple[int, int], Prime]:
 
 def prime(width: int, seed: int = 0) -> Prime:
     return load_primes()[(width, seed)]
+
+
+def load_full_primes(path: str = PRIMES_JSON) -> dict[tuple[int, int], Prime]:
+    """Committed table of full-width primes (exactly W bits), keyed by (W, seed)."""
+    with open(path) as f:
+        doc = json.load(f)
+    out = {}
+    for e in doc.get("full_primes", []):
+        p = Prime(width=e["width"], seed=e["seed"], q=int(e["q"], 16), bits=e["bits"],
+                  two_adicity=e["two_adicity"])
+        out[(p.width, p.seed)] = p
+    return out
+
+
+def prime_full(width: int, seed: int = 0) -> Prime:
+    return load_full_primes()[(width, seed)]
 
 
 # ----------------------------------------------------------------------------- residues

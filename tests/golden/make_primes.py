@@ -1,6 +1,8 @@
 """Writes tests/golden/primes.json: seed-generated NTT-friendly primes per width.
 
-Calls only the oracle (gen_prime, two_adicity).  Run from the repository root:
+Two tables: moduli of W-4 bits (Barrett contexts) and full-width moduli of W bits
+(Montgomery contexts).  Calls only the oracle (gen_prime, gen_prime_full, two_adicity).
+Run from the repository root:
     python tests/golden/make_primes.py
 """
 import json
@@ -8,7 +10,7 @@ import os
 import sys
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))))
-from oracle import gen_prime, two_adicity  # noqa: E402
+from oracle import gen_prime, gen_prime_full, two_adicity  # noqa: E402
 
 WIDTHS = (128, 256, 384, 768)
 SEEDS = (0, 1, 2, 3)
@@ -24,6 +26,14 @@ def main():
             q = gen_prime(w, s)
             out["primes"].append({"width": w, "seed": s, "q": hex(q), "bits": q.bit_length(),
                                   "two_adicity": two_adicity(q)})
+    out["full_comment"] = ("q = c*2^32 + 1 with exactly W bits (full-width modulus); c from "
+                           "random.Random('moma-full:<W>:<seed>'); Miller-Rabin accepted; oracle.gen_prime_full")
+    out["full_primes"] = []
+    for w in WIDTHS:
+        for s in SEEDS[:2]:
+            q = gen_prime_full(w, s)
+            out["full_primes"].append({"width": w, "seed": s, "q": hex(q), "bits": q.bit_length(),
+                                       "two_adicity": two_adicity(q)})
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "primes.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)

@@ -305,6 +305,55 @@ def test_barrett_needs_full_bit_length():
     assert worst >= 2
 
 
+# ------------------------------------------------------------------ full-width moduli (Montgomery)
+
+def test_full_width_primes_table():
+    table = inputs.load_full_primes()
+    assert len(table) == 8
+    for (w, s), p in table.items():
+        assert sympy.isprime(p.q), (w, s)
+        assert p.q.bit_length() == w == p.bits                 # fills the container
+        assert (p.q - 1) % (1 << 32) == 0 and p.two_adicity >= 32
+        assert oracle.gen_prime_full(w, s) == p.q
+
+
+@pytest.mark.parametrize("width", [128, 256, 384, 768])
+def test_montgomery_redc_is_multiplication_by_r_inverse(width):
+    """REDC(T) = T R^-1 mod q (sympy's modular inverse), below 2q before its correction."""
+    R = 1 << width
+    rng = random.Random(width)
+    for q in (inputs.prime_full(width).q, inputs.prime_full(width, 1).q, inputs.prime(width).q):
+        rinv = int(sympy.mod_inverse(R, q))
+        qi = oracle.montgomery_qinv_word(q)
+        assert (q * qi + 1) % (1 << 32) == 0
+        for T in [0, 1, q - 1, q, q * R - 1, (q - 1) * (q - 1)] + [rng.randrange(q * R) for _ in range(200)]:
+            raw = oracle.montgomery_redc_words(T, q, width, final=False)
+            assert 0 <= raw < 2 * q
+            r = oracle.montgomery_redc_words(T, q, width)
+            assert r == T * rinv % q
+            assert (r * R - T) % q == 0
+
+
+@pytest.mark.parametrize("width", [128, 256, 384, 768])
+def test_mulmod_via_montgomery_is_the_product(width):
+    rng = random.Random(3 * width)
+    q = inputs.prime_full(width).q
+    edge = [0, 1, 2, q - 1, q - 2, (1 << (width - 1)) % q, q // 2]
+    pairs = [(a, b) for a in edge for b in edge] + [(rng.randrange(q), rng.randrange(q)) for _ in range(300)]
+    for a, b in pairs:
+        assert oracle.mulmod_via_montgomery(a, b, q, width) == a * b % q
+        assert oracle.montgomery_mul(a, b, q, width) == a * b * int(sympy.mod_inverse(1 << width, q)) % q
+
+
+def test_full_width_transform_roots():
+    for w in (128, 256, 384, 768):
+        q = inputs.prime_full(w).q
+        for lg in (1, 12, 24):
+            n = 1 << lg
+            wn = oracle.root_of_unity(q, n)
+            assert pow(wn, n, q) == 1 and pow(wn, n // 2, q) == q - 1
+
+
 # ------------------------------------------------------------------ representation
 
 def test_digit_order_fixture():
