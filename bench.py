@@ -39,8 +39,8 @@ L = WIDTH // 32
 # DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20)
 # from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule
 # and kernel version (None otherwise).
-NTT_PASS_TRAFFIC_BYTES = None
-NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 1, "tile_log": 10, "max_logr": 5, "cta_threads": 128, "tight_regs": 0}
+NTT_PASS_TRAFFIC_BYTES = 970_370_048
+NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 2, "tile_log": 10, "max_logr": 5, "cta_threads": 128, "tight_regs": 0}
 
 # Integer-multiply peak from the unit counts: the multiply pipe (fmaheavy) of each of the 4 SM
 # sub-partitions takes one whole 32x32->64 product (mad.wide) per 4 cycles per warp, i.e. 8 lane
@@ -468,11 +468,12 @@ def run_uneven_batch(steps, warmup, n_jobs=256, seed=0):
 def run_sensitivity(steps=5):
     """Sec. 5.4 analogues: (1) forward NTT runtime against width at n = 4096 (batches of 256,
     ns per butterfly = 2t/(n log2 n) as in Sec. 5.3); (2) mulmod with schoolbook carry chains,
-    whole mad.wide products and Karatsuba (Eq. mulk) at each width, 2^22 elements."""
+    whole mad.wide products and Karatsuba (Eq. mulk) at each width, 2^22 elements; (3) the same
+    mulmod and transform over a full-width modulus (Montgomery products, Sec. 5.2)."""
     import torch
 
     from paper_2501_07535_gb300 import inputs, moma
-    out = {"ntt_n4096": [], "mulmod_engines": []}
+    out = {"ntt_n4096": [], "mulmod_engines": [], "full_width_montgomery": []}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def timed(fn):
@@ -510,6 +511,21 @@ def run_sensitivity(steps=5):
             eng[name] = round(vn / timed(lambda: moma.moma_vec_mulmod(ctx, vn, a, b, c)) / 1e6, 2)
         out["mulmod_engines"].append({"bits": w, "gelem_s": eng,
                                       "karatsuba_over_schoolbook": round(eng["karatsuba"] / eng["schoolbook_carry"], 3)})
+        # full-width modulus (W bits, Montgomery products) against the (W-4)-bit Barrett context
+        pf = inputs.prime_full(w)
+        fctx = moma.moma_ctx_create_full(pf.q, w)
+        fa = moma.to_device(inputs.residues(pf.q, pf.L, vn, 1))
+        fb = moma.to_device(inputs.residues(pf.q, pf.L, vn, 2))
+        mont_gelem = vn / timed(lambda: moma.moma_vec_mulmod(fctx, vn, fa, fb, c)) / 1e6
+        fx = torch.zeros_like(x)
+        fx[:, 0, :] = 3
+        fms = timed(lambda: moma.moma_ntt_fwd_many(fctx, n, cnt, fx, y))
+        out["full_width_montgomery"].append({
+            "bits": w, "mulmod_gelem_s": round(mont_gelem, 2),
+            "mulmod_over_barrett": round(mont_gelem / max(eng.values()), 3),
+            "ntt_n4096_ns_per_butterfly": round(fms * 1e6 / cnt * 2 / (n * 12), 4),
+            "ntt_over_barrett_time": round(fms / ms, 3)})
+        moma.moma_ctx_destroy(fctx)
         moma.moma_ctx_destroy(ctx)
     return out
 

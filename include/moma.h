@@ -16,7 +16,8 @@
  *   q must be odd and have exactly bits-4 bits (Sec. 5.2: a (k-4)-bit modulus for a
  *   k-bit container, which the Barrett constants of Sec. 3.1 need); otherwise
  *   MOMA_ERR_MODULUS.  Every width is supported by every call, except moma_ntt_fwd_noalloc
- *   (128 to 384 bits).
+ *   (128 to 384 bits).  Full-width moduli (up to all bits of the container) take
+ *   moma_ctx_create_full (Montgomery reduction); see there for the calls they support.
  * Layout.  A vector of n residues is limb-major: uint32 v[L][n], limb 0 the least
  *   significant word of each residue (the paper writes words most significant first;
  *   that is notation only).  Plane j of element i is at v[j*n + i].
@@ -70,6 +71,22 @@ const char *moma_status_string(moma_status s);
  * plans (twiddle tables) are built lazily per size.  *out receives the context; it is
  * set to NULL on error.  Uses the current CUDA device. */
 moma_status moma_ctx_create(const uint32_t *q, int bits, moma_ctx **out);
+
+/* Context for a full-width modulus: q odd, with more than bits-32 and at most `bits` bits
+ * (the top limb nonzero, up to a modulus that fills the container), else MOMA_ERR_MODULUS.
+ * Sec. 5.2 names Montgomery reduction for such moduli, where the 4 spare bits that the
+ * Barrett constants of Sec. 3.1 need are absent.  Every product is a word-serial Montgomery
+ * product (R = 2^bits, q' = -q^-1 mod 2^32, 2L^2 + L word products); sums form their carry
+ * word.  Inputs and outputs are canonical residues as for moma_ctx_create (no Montgomery form
+ * visible to the caller: mulmod is two Montgomery products, the second by R^2 mod q;
+ * twiddles, the axpy scalar and n^-1 are kept in Montgomery form internally).
+ * Supported: moma_vec_*, moma_ntt_fwd/inv, moma_ntt_{fwd,inv}_many, moma_polymul,
+ * moma_ntt_fwd_noalloc, moma_ctx_root, configuration and autotuning (the product engine
+ * setting is ignored).  Negacyclic calls and batch jobs give MOMA_ERR_UNSUPPORTED. */
+moma_status moma_ctx_create_full(const uint32_t *q, int bits, moma_ctx **out);
+
+/* 1 for a context made by moma_ctx_create_full, else 0 (also for NULL). */
+int moma_ctx_is_full(const moma_ctx *ctx);
 
 /* Release the context, its plans and device tables.  Safe on NULL.  The caller must
  * ensure no work using the context is still running. */
@@ -246,6 +263,8 @@ typedef enum {
 /* Schedule of one operation at one size.  Any field set to 0 means "library default".
  *   engine     1: word products as mad.lo/mad.hi carry chains (mad.lo.cc, madc.hi.cc);
  *              2: word products as mad.wide (whole 64-bit products, carry in the addend);
+ *              products by a fixed multiplicand (twiddles, the axpy scalar) form their
+ *              truncated high half this way and their low halves by carry chains;
  *              3: (MOMA_OP_MUL only) the double-width product a*b by Karatsuba (Sec. 2.2
  *              Eq. mulk) down to 4-limb carry-chain schoolbook products.
  *              1 and 2 compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd);

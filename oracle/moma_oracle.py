@@ -24,6 +24,9 @@ Readings where the paper is silent or inconsistent (each listed in the design doc):
     w_n = w_max^(2^s / n).
   * Moduli: q = c * 2^32 + 1 with exactly B bits, c drawn from a seeded generator,
     accepted by Miller-Rabin.
+  * Full-width moduli (B = W, Sec. 5.2 names Montgomery reduction for them without detail):
+    R = 2^W, REDC taken one 32-bit word at a time with q' = -q^-1 mod 2^32, one final
+    conditional subtraction; a product of canonical values is REDC(REDC(a b) (R^2 mod q)).
 """
 from __future__ import annotations
 

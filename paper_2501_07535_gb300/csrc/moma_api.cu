@@ -27,38 +27,48 @@ const char* moma_status_string(moma_status s) {
   return "MOMA_ERR_UNKNOWN";
 }
 
-moma_status moma_ctx_create(const uint32_t* q, int bits, moma_ctx** out) {
+// Common set-up of both context kinds.  mont: a full-width modulus reduced by Montgomery
+// products (Sec. 5.2); otherwise a (W-4)-bit modulus with the Barrett constants of Sec. 3.1.
+static moma_status ctx_create(const uint32_t* q, int bits, bool mont, moma_ctx** out) {
   if (!out) return MOMA_ERR_INVALID_ARG;
   *out = nullptr;
   if (!q) return MOMA_ERR_INVALID_ARG;
   if (bits != 128 && bits != 256 && bits != 384 && bits != 768) return MOMA_ERR_INVALID_ARG;
   const int L = bits / 32;
   BigU Q = BigU::from_words(q, L);
-  // Sec. 5.2: a (k-4)-bit modulus in a k-bit container; odd (needed by every reduction)
-  if (Q.bits() != bits - 4 || !Q.is_odd()) return MOMA_ERR_MODULUS;
+  if (!Q.is_odd()) return MOMA_ERR_MODULUS;  // odd: needed by every reduction
+  if (mont ? Q.bits() <= bits - 32 : Q.bits() != bits - 4) return MOMA_ERR_MODULUS;
   moma_ctx* c = new (std::nothrow) moma_ctx();
   if (!c) return MOMA_ERR_OOM;
   c->L = L;
   c->bits = bits;
+  c->mont = mont;
   c->Q = Q;
   c->red = new Reducer(Q);
   c->k.L = L;
-  const int B = bits - 4;
   BigU W = pow2(bits);
-  BigU nq = sub(W, Q);
-  BigU mu;
-  divmod(pow2(2 * B + 3), Q, &mu, nullptr);  // Eq. mu with k = 2B+3
-  BigU q2 = add(Q, Q);
-  BigU q4 = add(q2, q2);
   BigU Q0, R0;
   divmod(W, Q, &Q0, &R0);
   Q.to_words(c->k.q, L);
-  nq.to_words(c->k.nq, L);
-  mu.to_words(c->k.mu, L);
-  q2.to_words(c->k.q2, L);
-  q4.to_words(c->k.q4, L);
   R0.to_words(c->k.R0, L);
   c->k.Q0 = Q0.word(0);
+  if (mont) {
+    c->red->mulmod(R0, R0).to_words(c->k.r2, L);  // R^2 mod q
+    uint32_t inv = q[0];  // q^-1 mod 2^32 by Newton's iteration (q odd: q*q = 1 mod 8 to start)
+    for (int i = 0; i < 5; ++i) inv *= 2u - q[0] * inv;
+    c->k.qinv = 0u - inv;
+  } else {
+    const int B = bits - 4;
+    BigU nq = sub(W, Q);
+    BigU mu;
+    divmod(pow2(2 * B + 3), Q, &mu, nullptr);  // Eq. mu with k = 2B+3
+    BigU q2 = add(Q, Q);
+    BigU q4 = add(q2, q2);
+    nq.to_words(c->k.nq, L);
+    mu.to_words(c->k.mu, L);
+    q2.to_words(c->k.q2, L);
+    q4.to_words(c->k.q4, L);
+  }
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     delete c->red;
@@ -74,6 +84,16 @@ moma_status moma_ctx_create(const uint32_t* q, int bits, moma_ctx** out) {
   *out = c;
   return MOMA_OK;
 }
+
+moma_status moma_ctx_create(const uint32_t* q, int bits, moma_ctx** out) {
+  return ctx_create(q, bits, false, out);
+}
+
+moma_status moma_ctx_create_full(const uint32_t* q, int bits, moma_ctx** out) {
+  return ctx_create(q, bits, true, out);
+}
+
+int moma_ctx_is_full(const moma_ctx* ctx) { return ctx && ctx->mont ? 1 : 0; }
 
 void moma_ctx_destroy(moma_ctx* ctx) {
   if (!ctx) return;

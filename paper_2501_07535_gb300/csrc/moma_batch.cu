@@ -239,12 +239,8 @@ size_t vec_args(const moma_ctx* ctx, const moma_job& j, ArgBuf& ab) {
   a.c = j.out;
   a.n = j.n;
   a.op = (uint32_t)(j.op - MOMA_OP_ADD);
+  fill_modk<L>(ctx, a.k);
   for (int i = 0; i < L; ++i) {
-    a.k.q[i] = ctx->k.q[i];
-    a.k.nq[i] = ctx->k.nq[i];
-    a.k.mu[i] = ctx->k.mu[i];
-    a.k.q2[i] = ctx->k.q2[i];
-    a.k.q4[i] = ctx->k.q4[i];
     a.alpha[i] = 0;
     a.alphap[i] = 0;
   }
@@ -333,6 +329,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     moma_ctx* ctx = jb.ctx;
     if (!ctx || !jb.a || !jb.out) return MOMA_ERR_INVALID_ARG;
     if (ctx->device != dev) return MOMA_ERR_INVALID_ARG;
+    if (ctx->mont) return MOMA_ERR_UNSUPPORTED;  // full-width moduli: per-call API only
     const bool ntt = jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV || jb.op == MOMA_OP_POLYMUL;
     if (!ntt && (jb.op < MOMA_OP_ADD || jb.op > MOMA_OP_AXPY)) return MOMA_ERR_INVALID_ARG;
     if ((jb.op == MOMA_OP_POLYMUL || (!ntt)) && !jb.b) return MOMA_ERR_INVALID_ARG;

@@ -4,6 +4,7 @@
 // A thread handles V consecutive elements per step and reads each of the L planes with
 // one V-wide vector load (uint4 for V = 4), so every load of a warp is a coalesced
 // 32*V-word run of one plane.  Grid-stride loop over a grid sized to fill every SM.
+#include "moma_consts.cuh"
 #include "moma_internal.hpp"
 #include "moma_limbs.cuh"
 
@@ -44,7 +45,8 @@ struct VecT<4> {
 
 // ENG: 1 carry-chain rows, 2 whole-product (mad.wide) rows, 3 Karatsuba double-width product
 // (Eq. mulk, carry-chain base) for mulmod; axpy's fixed-scalar product has no double-width
-// product, so ENG 3 uses carry chains there.
+// product, so ENG 3 uses carry chains there.  ENG 4: full-width contexts (Montgomery products,
+// the sum's carry word formed; the axpy scalar arrives in Montgomery form).
 template <int L, int OP, int V, int ENG>
 __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArgs<L> p) {
   using VT = typename VecT<V>::T;
@@ -65,7 +67,19 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
     uint32_t z[V][L];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if constexpr (OP == VEC_ADD) {
+      if constexpr (ENG == 4) {
+        if constexpr (OP == VEC_ADD) {
+          addmod_full<L>(z[v], x[v], y[v], p.k.q);
+        } else if constexpr (OP == VEC_SUB) {
+          submod<L>(z[v], x[v], y[v], p.k.q);
+        } else if constexpr (OP == VEC_MUL) {
+          mulmod_mont<L>(z[v], x[v], y[v], p.k);
+        } else {
+          uint32_t ax[L];
+          montmul<L>(ax, x[v], p.alpha, p.k);
+          addmod_full<L>(z[v], ax, y[v], p.k.q);
+        }
+      } else if constexpr (OP == VEC_ADD) {
         addmod<L>(z[v], x[v], y[v], p.k.q);
       } else if constexpr (OP == VEC_SUB) {
         submod<L>(z[v], x[v], y[v], p.k.q);
@@ -95,20 +109,20 @@ static moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uin
   p.b = b;
   p.c = c;
   p.n = n;
+  fill_modk<L>(ctx, p.k);
   for (int i = 0; i < L; ++i) {
-    p.k.q[i] = ctx->k.q[i];
-    p.k.nq[i] = ctx->k.nq[i];
-    p.k.mu[i] = ctx->k.mu[i];
-    p.k.q2[i] = ctx->k.q2[i];
-    p.k.q4[i] = ctx->k.q4[i];
     p.alpha[i] = 0;
     p.alphap[i] = 0;
   }
   if (OP == VEC_AXPY) {
     BigU al = BigU::from_words(alpha_host, L);
     if (cmp(al, ctx->Q) >= 0) return MOMA_ERR_INVALID_ARG;
-    al.to_words(p.alpha, L);
-    companion(ctx, al, p.alphap);
+    if (ENG == 4) {  // alpha R mod q: one Montgomery product gives alpha * x
+      ctx->red->mulmod(al, BigU::from_words(ctx->k.R0, L)).to_words(p.alpha, L);
+    } else {
+      al.to_words(p.alpha, L);
+      companion(ctx, al, p.alphap);
+    }
   }
   static int occ = -1;  // per-instantiation occupancy, computed once
   if (occ < 0) {
@@ -165,6 +179,15 @@ static moma_status dispatch_op(moma_ctx* ctx, int op, size_t n, const uint32_t* 
                                const uint32_t* alpha, const moma_config& cfg, cudaStream_t st) {
   const int eng = cfg.engine;
   const int vw = cfg.vec_width;
+  if (ctx->mont) {  // full-width modulus: Montgomery, one element per thread
+    switch (op) {
+      case VEC_ADD: return run_vec<L, VEC_ADD, 1, 4>(ctx, n, a, b, c, alpha, st);
+      case VEC_SUB: return run_vec<L, VEC_SUB, 1, 4>(ctx, n, a, b, c, alpha, st);
+      case VEC_MUL: return run_vec<L, VEC_MUL, 1, 4>(ctx, n, a, b, c, alpha, st);
+      case VEC_AXPY: return run_vec<L, VEC_AXPY, 1, 4>(ctx, n, a, b, c, alpha, st);
+    }
+    return MOMA_ERR_INVALID_ARG;
+  }
   switch (op) {
     case VEC_ADD: return dispatch_v<L, VEC_ADD, 1>(ctx, n, a, b, c, alpha, vw, st);
     case VEC_SUB: return dispatch_v<L, VEC_SUB, 1>(ctx, n, a, b, c, alpha, vw, st);

@@ -22,7 +22,9 @@ struct HostConsts {
   int L = 0;
   uint32_t q[kMaxL] = {}, nq[kMaxL] = {}, mu[kMaxL] = {}, q2[kMaxL] = {}, q4[kMaxL] = {};
   uint32_t R0[kMaxL] = {};  // 2^(32L) mod q
-  uint32_t Q0 = 0;          // floor(2^(32L) / q)  (between 16 and 31)
+  uint32_t Q0 = 0;          // floor(2^(32L) / q)  (between 16 and 31 for a W-4 bit q)
+  uint32_t r2[kMaxL] = {};  // full-width contexts: 2^(64L) mod q
+  uint32_t qinv = 0;        // full-width contexts: -q^-1 mod 2^32
 };
 
 // One Stockham pass: radix 2^logR over groups of stride n/R, after logNs radix bits.
@@ -50,6 +52,7 @@ struct Plan {
 struct moma_ctx {
   int L = 0;
   int bits = 0;
+  bool mont = false;  // full-width modulus: Montgomery reduction, canonical values
   int device = 0;
   int num_sms = 0;
   moma::HostConsts k;

@@ -395,11 +395,13 @@ MOMA_DEV void mul_full_k(uint32_t (&t)[2 * L], const uint32_t (&x)[L], const uin
 // Kernel-parameter copy of the constants of one modulus (lives in the constant bank).
 template <int L>
 struct ModK {
-  uint32_t q[L];    // modulus, B = 32L - 4 bits
+  uint32_t q[L];    // modulus, B = 32L - 4 bits (full-width contexts: up to 32L bits)
   uint32_t nq[L];   // 2^(32L) - q, so that  t - s*q = t + s*nq  mod 2^(32L)
   uint32_t mu[L];   // Barrett constant floor(2^(2B+3) / q)  (Eq. mu, k = 2B+3)
   uint32_t q2[L];   // 2q
   uint32_t q4[L];   // 4q: bound of the lazy (not fully reduced) values inside a transform
+  uint32_t r2[L];   // full-width contexts: R^2 mod q, R = 2^(32L)
+  uint32_t qinv;    // full-width contexts: -q^-1 mod 2^32
 };
 
 // ------------------------------------------------------------------ Sec. 3.1, Eq. barrett
@@ -457,12 +459,9 @@ MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uin
 //   s = floor(a*wp / 2^(32L)) (truncated, exact or one less);  r = a*w - s*q mod 2^(32L).
 // For any a < 2^(32L): a*w/q - s < 3, so r lies in [0, 3q), which fits the container.
 // Used for twiddle factors (tables carry the companion) and for the axpy scalar.
-#ifndef MOMA_FIXED_HI_WIDE
-#define MOMA_FIXED_HI_WIDE 1
-#endif
-#ifndef MOMA_FIXED_LO_WIDE
-#define MOMA_FIXED_LO_WIDE 1
-#endif
+// WIDE: the truncated high half a*wp by whole mad.wide products, the two low halves by carry
+// chains (on GB300 2-3% faster than either form throughout: it splits the work between the
+// multiply pipe and the integer ALU pipe).
 template <int L, bool WIDE = false>
 MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
                                 const uint32_t (&wp)[L], const ModK<L>& k) {
@@ -470,15 +469,9 @@ MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const 
 #pragma unroll
   for (int i = 0; i < L; ++i) r[i] = 0u;
   if constexpr (WIDE) {
-    if constexpr (MOMA_FIXED_HI_WIDE) mul_hi_trunc_w<L>(s, a, wp);
-    else mul_hi_trunc<L>(s, a, wp);
-    if constexpr (MOMA_FIXED_LO_WIDE) {
-      mul_lo_acc_w<L>(r, a, w);
-      mul_lo_acc_w<L>(r, s, k.nq);
-    } else {
-      mul_lo_acc<L>(r, a, w);
-      mul_lo_acc<L>(r, s, k.nq);
-    }
+    mul_hi_trunc_w<L>(s, a, wp);
+    mul_lo_acc<L>(r, a, w);
+    mul_lo_acc<L>(r, s, k.nq);
   } else {
     mul_hi_trunc<L>(s, a, wp);
     mul_lo_acc<L>(r, a, w);
@@ -493,6 +486,66 @@ MOMA_DEV void mulmod_fixed(uint32_t (&r)[L], const uint32_t (&a)[L], const uint3
   mulmod_fixed_lazy<L, WIDE>(r, a, w, wp, k);
   cond_sub<L>(r, k.q2);  // [0,3q) -> [0,2q)
   cond_sub<L>(r, k.q);   // -> [0,q)
+}
+
+// ------------------------------------------------------------------ full-width moduli
+// A modulus that fills its container (up to B = W bits) leaves no headroom: a + b can carry out
+// of the W bits, and the Barrett constants above no longer fit.  Sec. 5.2 names Montgomery
+// reduction for this case.  Values stay canonical; R = 2^W.
+
+// c = a + b mod q for canonical a, b < q < 2^W: the carry word of rule (moddq_add) is formed
+// (the sum may need W+1 bits); subtract q when the sum carried out or is >= q.
+template <int L>
+MOMA_DEV void addmod_full(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L], const uint32_t* q) {
+  add_words<L, false>(c, a, b);
+  const uint32_t carry = carry_out();
+  uint32_t d[L];
+  sub_words<L, false>(d, c, q);
+  const uint32_t keep = borrow_mask() & (carry - 1u);  // keep the sum: it borrowed and did not carry
+#pragma unroll
+  for (int i = 0; i < L; ++i) c[i] = (c[i] & keep) | (d[i] & ~keep);
+}
+
+// Montgomery product c = a b R^-1 mod q for a, b < q (operand scanning, 32-bit words): for each
+// word a_i, t += a_i b, then m = t_0 q' mod 2^32 and t += m q, which clears t_0, and t is shifted
+// down one word.  t stays below 2q (L+1 words; one more word holds the carries in between), so
+// one conditional subtraction ends it.  2L^2 + L word products.
+template <int L>
+MOMA_DEV void montmul(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L], const ModK<L>& k) {
+  uint32_t t[L + 2];
+#pragma unroll
+  for (int i = 0; i < L + 2; ++i) t[i] = 0u;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    row_lo<L, true>(t, a[i], b);
+    t[L] = addc_cc(t[L], 0u);
+    t[L + 1] = addc(t[L + 1], 0u);
+    row_hi<L, true>(t + 1, a[i], b);
+    t[L + 1] = addc(t[L + 1], 0u);
+    const uint32_t m = t[0] * k.qinv;
+    row_lo<L, true>(t, m, k.q);
+    t[L] = addc_cc(t[L], 0u);
+    t[L + 1] = addc(t[L + 1], 0u);
+    row_hi<L, true>(t + 1, m, k.q);
+    t[L + 1] = addc(t[L + 1], 0u);
+#pragma unroll
+    for (int j = 0; j <= L; ++j) t[j] = t[j + 1];
+    t[L + 1] = 0u;
+  }
+  uint32_t d[L];
+  sub_words<L, false>(d, t, k.q);
+  const uint32_t borrow = borrow_mask();
+  const uint32_t keep = borrow & (0u - (uint32_t)(t[L] == 0u));  // t < q: no carry word, and it borrowed
+#pragma unroll
+  for (int i = 0; i < L; ++i) c[i] = (t[i] & keep) | (d[i] & ~keep);
+}
+
+// c = a b mod q for canonical a, b: REDC(REDC(a b) (R^2 mod q)).
+template <int L>
+MOMA_DEV void mulmod_mont(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L], const ModK<L>& k) {
+  uint32_t t[L];
+  montmul<L>(t, a, b, k);
+  montmul<L>(c, t, k.r2, k);
 }
 
 }  // namespace moma

@@ -35,17 +35,17 @@ constexpr int kNttMaxThreads = 256;  // per CTA; the launch may use 32, 64, 128 
 
 // Default schedule per width, the fastest measured on GB300 for 2^20-point transforms in
 // batches (see the autotuner for other sizes): 128-thread CTAs on 2^10-element tiles with radix
-// up to 2^5 through 384 bits, 256-thread CTAs on 2^11 tiles with radix 2^7 at 768 bits;
-// whole-product rows at 128 bits, carry chains above.
+// up to 2^5 through 384 bits (the 384-bit kernel capped at 102 registers), 256-thread CTAs on
+// 2^11 tiles with radix 2^7 at 768 bits; the wide engine through 384 bits, carry chains at 768.
 struct NttDefaults {
-  int engine, tile_log, max_logr, threads;
+  int engine, tile_log, max_logr, threads, tight;
 };
 static NttDefaults ntt_defaults(int L) {
   switch (L) {
-    case 4: return {2, 10, 5, 128};
-    case 8: return {1, 10, 5, 128};
-    case 12: return {1, 10, 5, 128};
-    default: return {1, 11, 7, 256};
+    case 4: return {2, 10, 5, 128, 0};
+    case 8: return {2, 10, 5, 128, 0};
+    case 12: return {2, 10, 5, 128, 1};
+    default: return {1, 11, 7, 256, 0};
   }
 }
 int default_tile_log(int L) { return ntt_defaults(L).tile_log; }
@@ -66,6 +66,7 @@ moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
   if (c.tile_log == 0) c.tile_log = d.tile_log;
   if (c.max_logr == 0) c.max_logr = c.tile_log == d.tile_log ? d.max_logr : (c.tile_log > 6 ? c.tile_log - 5 : 1);
   if (c.cta_threads == 0) c.cta_threads = d.threads;
+  if (it == ctx->configs.end() && c.cta_threads <= 128) c.tight_regs = d.tight;
   c.vec_width = 0;
   return c;
 }
@@ -82,18 +83,23 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
   return true;
 }
 
-// Register cap: 128 per thread up to 384 bits (two 256-thread CTAs per SM at least); the
-// 768-bit kernel needs the full 255.  TIGHT variants (at most 128 threads per CTA) are compiled
+// Register cap: 85 per thread up to 384 bits (six 128-thread or three 256-thread CTAs per SM;
+// measured 2-4% faster than 128); the 768-bit kernel needs the full 255.  TIGHT variants (at most 128 threads per CTA) are compiled
 // for 64 registers up to 256 bits and 102 at 384 bits, without spills, for more resident CTAs.
-#ifndef MOMA_NTT_MINB
-#define MOMA_NTT_MINB 3
-#endif
 template <int L, bool WIDE, bool TIGHT>
 __global__ void __launch_bounds__(TIGHT ? 128 : kNttMaxThreads,
-                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 1)) : (L <= 12 ? MOMA_NTT_MINB : 1))
+                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 1)) : (L <= 12 ? 3 : 1))
     ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ __align__(16) uint32_t sm[];
   ntt_tile<L, WIDE>(p, blockIdx.x, sm);
+}
+
+// Full-width contexts: the same pass with Montgomery arithmetic (carry chains, canonical values).
+template <int L>
+__global__ void __launch_bounds__(kNttMaxThreads, L <= 12 ? 2 : 1)
+    ntt_pass_mont_kernel(const __grid_constant__ NttPassArgs<L> p) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  ntt_tile_impl<L, MontArith<L>>(p, blockIdx.x, sm);
 }
 
 // ------------------------------------------------------------------ twiddle tables
@@ -111,7 +117,9 @@ struct TwGenArgs {
   ModK<L> k;
 };
 
-template <int L>
+// MONT: full-width context; pw, init and the entries are in Montgomery form (x R mod q), the
+// products are Montgomery products and the companion half of each entry is zero.
+template <int L, bool MONT>
 __global__ void __launch_bounds__(256) twiddle_gen_kernel(const __grid_constant__ TwGenArgs<L> p) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < p.count; idx += stride) {
@@ -122,10 +130,19 @@ __global__ void __launch_bounds__(256) twiddle_gen_kernel(const __grid_constant_
     for (uint32_t bb = 0; bb < p.logn; ++bb) {
       if ((e >> bb) & 1) {
         uint32_t t[L];
-        mulmod_barrett<L>(t, acc, p.pw[bb], p.k);
+        if constexpr (MONT) montmul<L>(t, acc, p.pw[bb], p.k);
+        else mulmod_barrett<L>(t, acc, p.pw[bb], p.k);
 #pragma unroll
         for (int l = 0; l < L; ++l) acc[l] = t[l];
       }
+    }
+    if constexpr (MONT) {
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        p.dst[idx * 2 * L + l] = acc[l];
+        p.dst[idx * 2 * L + L + l] = 0u;
+      }
+      continue;
     }
     // companion floor(w*2^W/q) = w*Q0 + floor(w*R0/q), with 2^W = Q0*q + R0
     uint32_t prod[2 * L], rem[L], quo[L];
@@ -148,17 +165,6 @@ __global__ void __launch_bounds__(256) twiddle_gen_kernel(const __grid_constant_
 }
 
 template <int L>
-static void fill_modk(const moma_ctx* ctx, ModK<L>& k) {
-  for (int i = 0; i < L; ++i) {
-    k.q[i] = ctx->k.q[i];
-    k.nq[i] = ctx->k.nq[i];
-    k.mu[i] = ctx->k.mu[i];
-    k.q2[i] = ctx->k.q2[i];
-    k.q4[i] = ctx->k.q4[i];
-  }
-}
-
-template <int L>
 static moma_status gen_table(const moma_ctx* ctx, uint32_t* dst, uint64_t count, uint64_t D, uint64_t C,
                              uint64_t S, int logn, const std::vector<BigU>& pw, const BigU& init) {
   TwGenArgs<L> a;
@@ -168,15 +174,20 @@ static moma_status gen_table(const moma_ctx* ctx, uint32_t* dst, uint64_t count,
   a.C = C;
   a.S = S;
   a.logn = (uint32_t)logn;
-  for (int b = 0; b <= kMaxLogN; ++b)
-    for (int l = 0; l < L; ++l) a.pw[b][l] = b < logn ? pw[b].word(l) : 0u;
-  init.to_words(a.init, L);
+  // full-width contexts take the factors in Montgomery form: x R mod q, R = 2^(32L)
+  auto form = [&](const BigU& x) { return ctx->mont ? ctx->red->mulmod(x, BigU::from_words(ctx->k.R0, L)) : x; };
+  for (int b = 0; b <= kMaxLogN; ++b) {
+    const BigU f = b < logn ? form(pw[b]) : BigU();
+    for (int l = 0; l < L; ++l) a.pw[b][l] = f.word(l);
+  }
+  form(init).to_words(a.init, L);
   for (int l = 0; l < L; ++l) a.R0[l] = ctx->k.R0[l];
   a.Q0 = ctx->k.Q0;
   fill_modk<L>(ctx, a.k);
   uint64_t blocks = (count + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  twiddle_gen_kernel<L><<<(unsigned)blocks, 256>>>(a);
+  if (ctx->mont) twiddle_gen_kernel<L, true><<<(unsigned)blocks, 256>>>(a);
+  else twiddle_gen_kernel<L, false><<<(unsigned)blocks, 256>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -297,8 +308,12 @@ static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_lo
   }
   BigU ninv = sub(ctx->Q, shr(sub(ctx->Q, BigU(1)), logn));  // n^-1 = q - (q-1)/n
   if (inverse) {
-    ninv.to_words(pl->scale, L);
-    companion(ctx, ninv, pl->scalep);
+    if (ctx->mont) {  // n^-1 R mod q (Montgomery form); no companion
+      ctx->red->mulmod(ninv, BigU::from_words(ctx->k.R0, L)).to_words(pl->scale, L);
+    } else {
+      ninv.to_words(pl->scale, L);
+      companion(ctx, ninv, pl->scalep);
+    }
   }
   if (nega) {
     // psi = primitive 2n-th root (psi^2 = w_n); forward table psi^e, inverse n^-1 psi^-e, e < n
@@ -328,6 +343,7 @@ moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int ma
   if (st) return st;
   if (logn > ctx->two_adicity || logn < 1 || logn > kMaxLogN) return MOMA_ERR_SIZE;
   if (nega && logn + 1 > ctx->two_adicity) return MOMA_ERR_SIZE;  // needs a 2n-th root
+  if (nega && ctx->mont) return MOMA_ERR_UNSUPPORTED;
   if (logn <= tile_log) max_logr = 0;  // single pass: the split does not matter
   std::lock_guard<std::mutex> g(ctx->lock);
   auto key = std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr, nega ? 1 : 0);
@@ -364,9 +380,38 @@ static moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, si
   return cuda_status(cudaGetLastError());
 }
 
+template <int L>
+static moma_status run_pass_mont(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
+                                 const uint32_t* src2, uint32_t* dst, uint32_t flags, int threads, cudaStream_t st) {
+  NttPassArgs<L> a;
+  fill_pass_args<L>(ctx, pl, d, count, src, src2, dst, flags, a);
+  const size_t smem = (size_t)L * 4u << (d.logR + d.logG);
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (cudaFuncSetAttribute(ntt_pass_mont_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             L * 4 << max_tile_log(L)) != cudaSuccess)
+      return MOMA_ERR_CUDA;
+    attr_done = true;
+  }
+  const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
+  if (grid == 0) return MOMA_OK;
+  if (grid > 0x7fffffffull) return MOMA_ERR_SIZE;
+  ntt_pass_mont_kernel<L><<<(unsigned)grid, threads, smem, st>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
 static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
                               const uint32_t* src2, uint32_t* dst, uint32_t flags, const moma_config& cfg,
                               cudaStream_t st) {
+  if (ctx->mont) {
+    switch (ctx->L) {
+      case 4: return run_pass_mont<4>(ctx, pl, d, count, src, src2, dst, flags, cfg.cta_threads, st);
+      case 8: return run_pass_mont<8>(ctx, pl, d, count, src, src2, dst, flags, cfg.cta_threads, st);
+      case 12: return run_pass_mont<12>(ctx, pl, d, count, src, src2, dst, flags, cfg.cta_threads, st);
+      case 24: return run_pass_mont<24>(ctx, pl, d, count, src, src2, dst, flags, cfg.cta_threads, st);
+    }
+    return MOMA_ERR_UNSUPPORTED;
+  }
   const bool wide = cfg.engine == 2;
   const int th = cfg.cta_threads;
   const bool tight = cfg.tight_regs != 0 && th <= 128 && ctx->L <= 12;

@@ -1,6 +1,7 @@
 // moma_ntt_tile.cuh -- one CTA tile of a Stockham NTT pass (device code shared by the
 // per-pass kernels of moma_ntt.cu and the persistent batch kernel of moma_batch.cu).
 #pragma once
+#include "moma_consts.cuh"
 #include "moma_internal.hpp"
 #include "moma_limbs.cuh"
 
@@ -108,12 +109,81 @@ __device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&
   for (int l = 0; l < L; ++l) a[l] = x[l];
 }
 
+// The modular arithmetic of a transform pass, by reduction.
+// Barrett contexts (B = W - 4): lazy values in [0, 4q) inside a transform, twiddles with Barrett
+// companions (mulmod_fixed_lazy), canonical store at the end.
+template <int L, bool WIDE>
+struct BarrettArith {
+  static __device__ __forceinline__ void pointwise(uint32_t (&v)[L], const uint32_t (&u)[L], const ModK<L>& k) {
+    uint32_t t[L];
+    mulmod_barrett<L, WIDE>(t, v, u, k);
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = t[l];
+  }
+  static __device__ __forceinline__ void mul_fixed(uint32_t (&v)[L], const uint32_t (&w)[L], const uint32_t (&wp)[L],
+                                                   const ModK<L>& k) {
+    uint32_t t[L];
+    mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, k);
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = t[l];
+  }
+  static __device__ __forceinline__ void butterfly(uint32_t (&a)[L], uint32_t (&b)[L], bool mul, const uint32_t* table,
+                                                   uint32_t entry, const ModK<L>& k) {
+    dif_butterfly_lazy<L, WIDE>(a, b, mul, table, entry, k);
+  }
+  static __device__ __forceinline__ void finish(uint32_t (&v)[L], const ModK<L>& k) {  // [0, 4q) -> [0, q)
+    cond_sub<L>(v, k.q2);
+    cond_sub<L>(v, k.q);
+  }
+};
+
+// Full-width contexts (up to B = W): canonical values throughout, twiddles and constants in
+// Montgomery form (w R mod q; the companion half of each table entry is unused), Montgomery
+// products.  The pointwise product of two canonical values is exact (mulmod_mont).
+template <int L>
+struct MontArith {
+  static __device__ __forceinline__ void pointwise(uint32_t (&v)[L], const uint32_t (&u)[L], const ModK<L>& k) {
+    uint32_t t[L];
+    mulmod_mont<L>(t, v, u, k);
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = t[l];
+  }
+  static __device__ __forceinline__ void mul_fixed(uint32_t (&v)[L], const uint32_t (&w)[L], const uint32_t (&wp)[L],
+                                                   const ModK<L>& k) {
+    (void)wp;
+    uint32_t t[L];
+    montmul<L>(t, v, w, k);
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = t[l];
+  }
+  static __device__ __forceinline__ void butterfly(uint32_t (&a)[L], uint32_t (&b)[L], bool mul, const uint32_t* table,
+                                                   uint32_t entry, const ModK<L>& k) {
+    uint32_t x[L], d[L];
+    addmod_full<L>(x, a, b, k.q);
+    submod<L>(d, a, b, k.q);
+    if (mul) {
+      uint32_t w[L], wp[L];
+      twiddle_load<L>(table, entry, w, wp);
+      montmul<L>(b, d, w, k);
+    } else {
+#pragma unroll
+      for (int l = 0; l < L; ++l) b[l] = d[l];
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) a[l] = x[l];
+  }
+  static __device__ __forceinline__ void finish(uint32_t (&v)[L], const ModK<L>& k) {
+    (void)v;
+    (void)k;
+  }
+};
+
 // One CTA tile of one Stockham pass: `tile` indexes (transform, group block).  `sm` holds
-// L*R*G words.  Used by the per-pass kernel and by the persistent batch kernel; source data
+// L*R*G words.  Used by the per-pass kernels and by the persistent batch kernel; source data
 // are read with L2-only loads so that data written earlier in the same persistent launch by
 // other SMs is never served from a stale L1 line.
-template <int L, bool WIDE>
-__device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm) {
+template <int L, class A>
+__device__ __forceinline__ void ntt_tile_impl(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm) {
   const uint32_t R = 1u << p.logR;
   const uint32_t G = 1u << p.logG;
   const uint32_t T = R << p.logG;
@@ -134,53 +204,35 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = __ldcg(p.src + idx + (uint64_t)l * p.n);
     if (p.flags & F_POINTWISE) {
-      uint32_t u[L], t[L];
+      uint32_t u[L];
 #pragma unroll
       for (int l = 0; l < L; ++l) u[l] = __ldcg(p.src2 + idx + (uint64_t)l * p.n);
-      mulmod_barrett<L, WIDE>(t, v, u, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
+      A::pointwise(v, u, p.k);
     }
-    if (p.flags & F_SCALE) {
-      uint32_t t[L];
-      mulmod_fixed_lazy<L, WIDE>(t, v, p.sc, p.scp, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
-    }
+    if (p.flags & F_SCALE) A::mul_fixed(v, p.sc, p.scp, p.k);
     if (p.flags & F_PSI_IN) {
-      uint32_t w[L], wp[L], t[L];
+      uint32_t w[L], wp[L];
       twiddle_load<L>(p.psi, j + (uint64_t)r * nR, w, wp);
-      mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
+      A::mul_fixed(v, w, wp, p.k);
     }
     if ((p.flags & F_PRETW) && r != 0 && (j & ns_mask) != 0) {
       const uint64_t ti = (uint64_t)(r - 1) * (ns_mask + 1) + (j & ns_mask);
-      uint32_t w[L], wp[L], t[L];
+      uint32_t w[L], wp[L];
       twiddle_load<L>(p.tw_pass, ti, w, wp);
-      mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
+      A::mul_fixed(v, w, wp, p.k);
     }
     tile_store<L>(sm, swz(e, logT), v);  // e = r*G + g
   }
   __syncthreads();
 
   // ---- R-point transforms: logR radix-2 DIF stages, in place in the tile
-#ifndef MOMA_STAGE_BALANCE
-#define MOMA_STAGE_BALANCE 1
-#endif
-#ifndef MOMA_STAGE_UNROLL
-#define MOMA_STAGE_UNROLL 1
-#endif
-  constexpr int kStageUnroll = MOMA_STAGE_UNROLL;
   const uint32_t logNT = 31u - (uint32_t)__clz(blockDim.x);
-  const uint32_t logW = (MOMA_STAGE_BALANCE && logNT > p.logG) ? logNT - p.logG : 0u;
+  const uint32_t logW = logNT > p.logG ? logNT - p.logG : 0u;
 #pragma unroll 1
   for (uint32_t s = 0; s < p.logR; ++s) {
     const uint32_t logh = p.logR - s - 1;
     const uint32_t h = 1u << logh;
-#pragma unroll kStageUnroll
+#pragma unroll 1
     for (uint32_t bi = threadIdx.x; bi < (T >> 1); bi += blockDim.x) {
       // butterfly row u of group g; the W = NT/G rows one pass of the CTA takes are rotated by
       // the pass index, so that every warp gets its share of the unit-twiddle (i = 0) rows
@@ -194,7 +246,7 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
       tile_load<L>(sm, a0, x0);
       tile_load<L>(sm, a1, x1);
       // twiddle w_(2h)^i = w_R^(i * R/(2h)); 1 for i = 0 and in the last stage (h = 1)
-      dif_butterfly_lazy<L, WIDE>(x0, x1, i != 0, p.tw_int, i << s, p.k);
+      A::butterfly(x0, x1, i != 0, p.tw_int, i << s, p.k);
       tile_store<L>(sm, a0, x0);
       tile_store<L>(sm, a1, x1);
     }
@@ -216,20 +268,20 @@ __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile,
     const uint32_t pr = __brev(sp) >> (32 - p.logR);
     uint32_t v[L];
     tile_load<L>(sm, swz((pr << p.logG) + g, logT), v);
-    if (p.flags & F_PSI_OUT) {  // [0, 4q) -> [0, 3q)
-      uint32_t w[L], wp[L], t[L];
+    if (p.flags & F_PSI_OUT) {  // Barrett: [0, 4q) -> [0, 3q)
+      uint32_t w[L], wp[L];
       twiddle_load<L>(p.psi, addr - base, w, wp);
-      mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, p.k);
-#pragma unroll
-      for (int l = 0; l < L; ++l) v[l] = t[l];
+      A::mul_fixed(v, w, wp, p.k);
     }
-    if (p.flags & F_LAST) {  // [0, 4q) -> [0, q)
-      cond_sub<L>(v, p.k.q2);
-      cond_sub<L>(v, p.k.q);
-    }
+    if (p.flags & F_LAST) A::finish(v, p.k);
 #pragma unroll
     for (int l = 0; l < L; ++l) p.dst[addr + (uint64_t)l * p.n] = v[l];
   }
+}
+
+template <int L, bool WIDE>
+__device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm) {
+  ntt_tile_impl<L, BarrettArith<L, WIDE>>(p, tile, sm);
 }
 
 // Host: fill the arguments of one pass (count transforms of length 2^logn).
@@ -253,12 +305,8 @@ inline void fill_pass_args(const moma_ctx* ctx, const Plan* pl, const PassDesc& 
   for (int i = 0; i < L; ++i) {
     a.sc[i] = pl->scale[i];
     a.scp[i] = pl->scalep[i];
-    a.k.q[i] = ctx->k.q[i];
-    a.k.nq[i] = ctx->k.nq[i];
-    a.k.mu[i] = ctx->k.mu[i];
-    a.k.q2[i] = ctx->k.q2[i];
-    a.k.q4[i] = ctx->k.q4[i];
   }
+  fill_modk<L>(ctx, a.k);
   (void)count;
 }
 

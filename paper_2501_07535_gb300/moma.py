@@ -40,6 +40,8 @@ _SZ = ctypes.c_size_t
 _SIGS = {
     "moma_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "moma_ctx_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "moma_ctx_create_full": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "moma_ctx_is_full": (ctypes.c_int, [_P]),
     "moma_ctx_destroy": (None, [_P]),
     "moma_ctx_limbs": (ctypes.c_int, [_P]),
     "moma_ctx_root": (ctypes.c_int, [_P, _SZ, _P]),
@@ -148,6 +150,19 @@ def moma_ctx_create(q: int, bits: int) -> int:
     qa = _limbs_array(q, L)
     _check(lib().moma_ctx_create(ctypes.cast(qa, _P), bits, ctypes.byref(h)), "moma_ctx_create")
     return h.value
+
+
+def moma_ctx_create_full(q: int, bits: int) -> int:
+    """Context for a full-width modulus (Montgomery reduction)."""
+    L = bits // 32
+    h = _P()
+    qa = _limbs_array(q, L)
+    _check(lib().moma_ctx_create_full(ctypes.cast(qa, _P), bits, ctypes.byref(h)), "moma_ctx_create_full")
+    return h.value
+
+
+def moma_ctx_is_full(ctx: int) -> int:
+    return lib().moma_ctx_is_full(ctx)
 
 
 def moma_ctx_destroy(ctx: int):

@@ -1,0 +1,171 @@
+"""Full-width moduli (W bits, Montgomery contexts) on the GPU, bit-exact against the oracle.
+
+The oracle computes the definitions (a + b, a - b, a * b, alpha * x + y mod q, Eq. ntt, the
+cyclic product); nothing on the GPU side is Barrett-specific here, every product is a
+Montgomery product.  Edge values include q - 1 (sums that carry out of the container) and
+residues with all-ones words.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2501_07535_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+WIDTHS = [128, 256, 384, 768]
+
+
+@pytest.fixture(scope="module")
+def fctx(gpu):
+    ctxs = {w: gpu.moma_ctx_create_full(inputs.prime_full(w).q, w) for w in WIDTHS}
+    yield ctxs
+    for h in ctxs.values():
+        gpu.moma_ctx_destroy(h)
+
+
+def _edge_values(q, W, rng, n):
+    L = W // 32
+    ones = (1 << (32 * (L - 1))) - 1  # all-ones low words
+    base = [0, 1, 2, q - 1, q - 2, q // 2, (q + 1) // 2, ones, q - ones, (1 << (W - 1)) % q]
+    vals = [base[i % len(base)] for i in range(n // 2)] + [rng.randrange(q) for _ in range(n - n // 2)]
+    rng.shuffle(vals)
+    return vals
+
+
+def test_create_full_checks_modulus(gpu):
+    assert gpu.moma_ctx_is_full(0) == 0
+    q = inputs.prime_full(256).q
+    with pytest.raises(gpu.MomaError):
+        gpu.moma_ctx_create_full(q + 1, 256)  # even
+    with pytest.raises(gpu.MomaError):
+        gpu.moma_ctx_create_full((1 << 200) + 1, 256)  # top limb empty
+    h = gpu.moma_ctx_create_full(inputs.prime(256).q, 256)  # a (W-4)-bit modulus is full-width too
+    try:
+        assert gpu.moma_ctx_is_full(h) == 1
+    finally:
+        gpu.moma_ctx_destroy(h)
+    with pytest.raises(gpu.MomaError):
+        gpu.moma_ctx_create(q, 256)  # the Barrett context keeps its W-4 bit contract
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("n", [1, 7, 1000, 4099])
+def test_full_width_blas(gpu, fctx, width, n):
+    import random
+    rng = random.Random(width * 7 + n)
+    q = inputs.prime_full(width).q
+    L = width // 32
+    a = _edge_values(q, width, rng, n)
+    b = _edge_values(q, width, rng, n)
+    alpha = rng.randrange(q)
+    da, db = gpu.to_device(inputs.from_ints(a, L)), gpu.to_device(inputs.from_ints(b, L))
+    h = fctx[width]
+    for name, fn, want in (("add", gpu.moma_vec_addmod, oracle.vec_addmod(a, b, q)),
+                           ("sub", gpu.moma_vec_submod, oracle.vec_submod(a, b, q)),
+                           ("mul", gpu.moma_vec_mulmod, oracle.vec_mulmod(a, b, q))):
+        dc = torch.empty_like(da)
+        fn(h, n, da, db, dc)
+        torch.cuda.synchronize()
+        assert inputs.to_ints(gpu.to_host(dc)) == want, name
+    dc = torch.empty_like(da)
+    gpu.moma_vec_axpymod(h, n, alpha, da, db, dc)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dc)) == oracle.vec_axpy(alpha, a, b, q)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_full_width_blas_large_sampled(gpu, fctx, width):
+    q = inputs.prime_full(width).q
+    L = width // 32
+    n = 1 << 20
+    a = inputs.residues(q, L, n, 1)
+    b = inputs.residues(q, L, n, 2)
+    da, db = gpu.to_device(a), gpu.to_device(b)
+    dc = torch.empty_like(da)
+    gpu.moma_vec_mulmod(fctx[width], n, da, db, dc)
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(width).choice(n, 2000, replace=False)
+    ai, bi = inputs.sample_ints(a, idx), inputs.sample_ints(b, idx)
+    got = inputs.sample_ints(gpu.to_host(dc), idx)
+    assert got == [x * y % q for x, y in zip(ai, bi)]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("lg", [1, 5, 10, 12, 13, 15])
+def test_full_width_ntt(gpu, fctx, width, lg):
+    if width == 768 and lg > 13:
+        pytest.skip("768-bit oracle transform at 2^15 is slow; 2^13 has the same two-pass split")
+    q = inputs.prime_full(width).q
+    L = width // 32
+    n = 1 << lg
+    x = inputs.residues(q, L, n, seed=lg + width)
+    xi = inputs.to_ints(x)
+    h = fctx[width]
+    dx = gpu.to_device(x)
+    dy, dz = torch.empty_like(dx), torch.empty_like(dx)
+    gpu.moma_ntt_fwd(h, n, dx, dy)
+    gpu.moma_ntt_inv(h, n, dy, dz)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(xi, q)
+    assert torch.equal(dz, dx)
+    w = gpu.moma_ctx_root(h, n)
+    assert w == oracle.root_of_unity(q, n)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("lg", [3, 11])
+def test_full_width_polymul_and_many(gpu, fctx, width, lg):
+    q = inputs.prime_full(width).q
+    L = width // 32
+    n = 1 << lg
+    a = inputs.residues(q, L, n, 5)
+    b = inputs.residues(q, L, n, 6)
+    ai, bi = inputs.to_ints(a), inputs.to_ints(b)
+    h = fctx[width]
+    da, db = gpu.to_device(a), gpu.to_device(b)
+    dc = torch.empty_like(da)
+    gpu.moma_polymul(h, n, da, db, dc)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dc)) == oracle.polymul_cyclic(ai, bi, q)
+    # three transforms in one call equal three single calls
+    xs = np.stack([inputs.residues(q, L, n, 40 + t) for t in range(3)])
+    dx = gpu.to_device(xs)
+    dy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd_many(h, n, 3, dx, dy)
+    torch.cuda.synchronize()
+    for t in range(3):
+        assert inputs.to_ints(gpu.to_host(dy[t])) == oracle.ntt_fwd(inputs.to_ints(xs[t]), q)
+
+
+def test_full_width_noalloc_and_refusals(gpu, fctx):
+    q = inputs.prime_full(256).q
+    h = fctx[256]
+    n = 1 << 12
+    x = gpu.to_device(inputs.residues(q, 8, n, 9))
+    want, got = torch.empty_like(x), torch.empty_like(x)
+    gpu.moma_ntt_fwd(h, n, x, want)
+    gpu.moma_ntt_fwd_noalloc(h, n, x, got)
+    torch.cuda.synchronize()
+    assert torch.equal(want, got)
+    with pytest.raises(gpu.MomaError) as ei:
+        gpu.moma_ntt_fwd_negacyclic(h, n, x, got)
+    assert ei.value.code == 9
+    with pytest.raises(gpu.MomaError) as ei:
+        gpu.moma_batch_create([{"op": "ntt_fwd", "ctx": h, "n": n, "a": x, "out": got}])
+    assert ei.value.code == 9
+
+
+def test_full_width_autotune(gpu, fctx):
+    q = inputs.prime_full(384).q
+    h = fctx[384]
+    n = 1 << 12
+    best, us = gpu.moma_autotune(h, "ntt_fwd", n, 2)
+    assert us > 0
+    x = inputs.residues(q, 12, n, 3)
+    dx = gpu.to_device(x)
+    dy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd(h, n, dx, dy)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), q)
