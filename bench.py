@@ -380,34 +380,60 @@ def run_ours(args):
 
 
 def run_profile(args):
-    """Small cases for ncu captures: batched forward NTTs (plan set-up call first), or the
-    2^24-element mulmod."""
+    """Small cases for ncu captures (each op: one untimed call first, then `steps` calls):
+    ntt: batched forward 256-bit 2^20 NTTs; mul / add / axpy: the 2^24-element 256-bit vector op;
+    ntt768: 768-bit 2^16 NTTs (batch 8); mont_ntt / mont_mul: the 256-bit NTT and mulmod over a
+    full-width modulus; batch: the uneven batch at reduced sizes (2^10..2^16, 64 jobs)."""
     import numpy as np
     import torch
 
-    from paper_2501_07535_gb300 import build, inputs, moma
+    from paper_2501_07535_gb300 import batch, build, inputs, moma
     build.build()
-    q = inputs.prime(WIDTH).q
-    n = 1 << LOGN
-    ctx = moma.moma_ctx_create(q, WIDTH)
-    if args.profile_op == "mul":
-        a = moma.to_device(inputs.residues(q, L, VEC_N, seed=1))
-        b = moma.to_device(inputs.residues(q, L, VEC_N, seed=2))
+    op = args.profile_op
+    if op == "batch":
+        jobs = inputs.uneven_batch(n_jobs=64, seed=0, log_n_range=(10, 16))
+        js = batch.JobSet(jobs)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            for _ in range(1 + args.steps):
+                js.run_batched(st)
+        st.synchronize()
+        status = js.status()
+        js.close()
+        js.ctx.close()
+        print(json.dumps({"profile": "batch", "jobs": 64, "calls": 1 + args.steps, "status": status}))
+        return
+    full = op.startswith("mont_")
+    width = 768 if op == "ntt768" else WIDTH
+    p = inputs.prime_full(width) if full else inputs.prime(width)
+    q, Lw = p.q, p.L
+    ctx = (moma.moma_ctx_create_full if full else moma.moma_ctx_create)(q, width)
+    if op in ("mul", "add", "axpy", "mont_mul"):
+        a = moma.to_device(inputs.residues(q, Lw, VEC_N, seed=1))
+        b = moma.to_device(inputs.residues(q, Lw, VEC_N, seed=2))
         c = torch.empty_like(a)
+        alpha = inputs.scalar_residue(q, 3)
         for _ in range(1 + args.steps):
-            moma.moma_vec_mulmod(ctx, VEC_N, a, b, c)
+            if op == "add":
+                moma.moma_vec_addmod(ctx, VEC_N, a, b, c)
+            elif op == "axpy":
+                moma.moma_vec_axpymod(ctx, VEC_N, alpha, a, b, c)
+            else:
+                moma.moma_vec_mulmod(ctx, VEC_N, a, b, c)
         torch.cuda.synchronize()
         moma.moma_ctx_destroy(ctx)
-        print(json.dumps({"profile": "vec_mulmod", "n": VEC_N, "calls": 1 + args.steps}))
+        print(json.dumps({"profile": op, "n": VEC_N, "calls": 1 + args.steps}))
         return
-    xs = np.stack([inputs.residues(q, L, n, seed=10 + t) for t in range(args.ntt_batch)])
+    n = 1 << (16 if op == "ntt768" else LOGN)
+    xs = np.stack([inputs.residues(q, Lw, n, seed=10 + t) for t in range(args.ntt_batch)])
     dx = moma.to_device(xs)
     dy = torch.empty_like(dx)
     for _ in range(1 + args.steps):
         moma.moma_ntt_fwd_many(ctx, n, args.ntt_batch, dx, dy)
     torch.cuda.synchronize()
     moma.moma_ctx_destroy(ctx)
-    print(json.dumps({"profile": "ntt_fwd_many", "n": n, "batch": args.ntt_batch, "calls": 1 + args.steps}))
+    print(json.dumps({"profile": op, "n": n, "batch": args.ntt_batch, "calls": 1 + args.steps}))
+    return
 
 
 def _pass_count(cfg, logn):
@@ -604,7 +630,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="small NTT-only case for ncu captures")
     ap.add_argument("--ntt-batch", type=int, default=8)
-    ap.add_argument("--profile-op", default="ntt", choices=["ntt", "mul"])
+    ap.add_argument("--profile-op", default="ntt",
+                    choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "batch"])
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

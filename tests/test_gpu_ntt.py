@@ -117,6 +117,34 @@ def test_ntt_256bit_2p20_full(gpu, ctxs):
     assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
 
 
+def test_ntt_bench_launch_configuration(gpu, ctxs):
+    """The benchmark's launch: 16 transforms of 2^20 points over the 256-bit prime in one
+    moma_ntt_fwd_many call with the default schedule.  The first transform is compared with the
+    oracle in full, every transform on sampled outputs (Horner, Eq. ntt at one k) and against
+    its own single-transform call."""
+    p = inputs.prime(256)
+    n, count = 1 << 20, 16
+    xs = np.stack([inputs.residues(p.q, p.L, n, seed=10 + t) for t in range(count)])
+    dx = gpu.to_device(xs)
+    dy = torch.empty_like(dx)
+    gpu.moma_ntt_fwd_many(ctxs[256], n, count, dx, dy)
+    torch.cuda.synchronize()
+    got = gpu.to_host(dy)
+    w = oracle.root_of_unity(p.q, n)
+    x0 = inputs.to_ints(xs[0])
+    assert inputs.to_ints(got[0]) == oracle.ntt_fwd(x0, p.q)
+    rng = np.random.Generator(np.random.PCG64(20))
+    single = torch.empty_like(dx[0])
+    for t in range(1, count):
+        gpu.moma_ntt_fwd(ctxs[256], n, dx[t], single)
+        torch.cuda.synchronize()
+        assert torch.equal(single, dy[t]), t
+        if t % 5 == 1:
+            xi = inputs.to_ints(xs[t])
+            k = int(rng.integers(0, n))
+            assert inputs.sample_ints(got[t], [k]) == [oracle.ntt_eval_at(xi, p.q, k, w)], (t, k)
+
+
 @pytest.mark.parametrize("width,lg", [(256, 24), (384, 24), (768, 20)])
 def test_ntt_2p24_sampled_and_roundtrip(gpu, ctxs, width, lg):
     p = inputs.prime(width)
