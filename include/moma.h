@@ -197,9 +197,9 @@ moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, ui
  * (out = a * b mod (x^n - 1, q)), MOMA_OP_ADD / SUB / MUL (out = a op b), MOMA_OP_AXPY
  * (out = alpha * a + b, alpha a HOST array of L limbs).  Device vectors follow the
  * conventions above; each job uses its own context (any widths and moduli may be mixed).
- * Transforms at 128 to 384 bits and vector ops at every width are tiles of the persistent
- * launch; 768-bit transform jobs run as per-pass launches right after it, on the same stream
- * (and in the same CUDA graph). */
+ * Jobs at 128 to 384 bits are tiles of the persistent launch; 768-bit jobs run with the
+ * per-call kernels right after it, on the same stream (and in the same CUDA graph).
+ * Contexts made by moma_ctx_create_full are refused (MOMA_ERR_UNSUPPORTED). */
 typedef struct {
   int op;
   moma_ctx *ctx;

@@ -15,9 +15,9 @@
 //
 // Widths are mixed inside one launch: the CTA dispatches on the tile's limb count.  Products
 // use whole mad.wide rows up to 256 bits and carry chains at 384 bits (the faster form of each
-// width on GB300); results are identical either way.  768-bit transforms are not tiles of the
-// persistent kernel (their registers would cut the occupancy of every other tile): they run as
-// per-pass launches right after it, on the same stream and inside the same CUDA graph.
+// width on GB300); results are identical either way.  768-bit jobs are not tiles of the
+// persistent kernel (their registers would cut the occupancy of every other tile): they run with
+// the per-call kernels right after it, on the same stream and inside the same CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -91,44 +91,54 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __restrict__ segs, uint32_t nseg,
-                                                             uint32_t total, uint32_t* ctr, int* status,
-                                                             uint64_t wait_polls) {
+#ifndef MOMA_BATCH_MINB
+#define MOMA_BATCH_MINB 5
+#endif
+// A CTA claims its next tile (one atomic, one look-up in the tile -> segment table) while it
+// works on the current one, and waits for the next tile's dependencies right after publishing
+// the current one.  Shared state is double-buffered by iteration parity.  Progress: the lowest
+// unfinished tile depends only on finished tiles, and whichever resident CTA holds it (as its
+// current or its claimed next tile) reaches it, so every wait ends.
+__global__ void __launch_bounds__(kBatchThreads, MOMA_BATCH_MINB)
+    batch_kernel(const Seg* __restrict__ segs, const uint32_t* __restrict__ tile_seg, uint32_t total, uint32_t* ctr,
+                 int* status, uint64_t wait_polls) {
   extern __shared__ __align__(16) uint32_t sm[];
-  __shared__ uint32_t s_tile, s_seg, s_skip;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const uint32_t t = atomicAdd(&ctr[0], 1u);
-      s_tile = t;
-      s_skip = 0;
-      if (t < total) {
-        uint32_t lo = 0, hi = nseg - 1;  // last segment with first <= t
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (segs[mid].first <= t) lo = mid;
-          else hi = mid - 1;
+  __shared__ uint32_t s_tile[2], s_seg[2], s_skip[2];
+  auto claim = [&](int b) {  // thread 0
+    const uint32_t t = atomicAdd(&ctr[0], 1u);
+    s_tile[b] = t;
+    s_seg[b] = t < total ? __ldg(tile_seg + t) : 0u;
+  };
+  auto wait_deps = [&](int b) {  // thread 0: bounded waits on the tile's dependency counters
+    s_skip[b] = 0;
+    if (s_tile[b] >= total) return;
+    const Seg& sg = segs[s_seg[b]];
+    for (int w = 0; w < 2; ++w) {
+      if (sg.wait_count[w] == 0) continue;
+      uint64_t polls = 0;
+      while (ld_acquire(&ctr[1 + sg.wait_id[w]]) < sg.wait_count[w]) {
+        if (++polls > wait_polls) {
+          atomicExch(status, (int)MOMA_ERR_TIMEOUT);
+          s_skip[b] = 1;
+          break;
         }
-        s_seg = lo;
-        const Seg& sg = segs[lo];
-        for (int w = 0; w < 2; ++w) {
-          if (sg.wait_count[w] == 0) continue;
-          uint64_t polls = 0;
-          while (ld_acquire(&ctr[1 + sg.wait_id[w]]) < sg.wait_count[w]) {
-            if (++polls > wait_polls) {
-              atomicExch(status, (int)MOMA_ERR_TIMEOUT);
-              s_skip = 1;
-              break;
-            }
-            __nanosleep(128);
-          }
-        }
+        __nanosleep(128);
       }
     }
-    __syncthreads();
-    const uint32_t t = s_tile;
+  };
+  if (threadIdx.x == 0) {
+    claim(0);
+    wait_deps(0);
+  }
+  __syncthreads();
+  for (int b = 0;; b ^= 1) {
+    const uint32_t t = s_tile[b];
     if (t >= total) return;
-    const Seg sg = segs[s_seg];
-    if (!s_skip) {
+    const uint32_t si = s_seg[b];
+    const bool skip = s_skip[b] != 0;
+    if (threadIdx.x == 0) claim(b ^ 1);
+    const Seg sg = segs[si];
+    if (!skip) {
       const uint32_t local = t - sg.first;
       if (sg.kind == SEG_NTT) {
         switch (sg.L) {
@@ -141,7 +151,6 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __re
           case 4: vec_tile<4>(*static_cast<const VecJobArgs<4>*>(sg.args), local); break;
           case 8: vec_tile<8>(*static_cast<const VecJobArgs<8>*>(sg.args), local); break;
           case 12: vec_tile<12>(*static_cast<const VecJobArgs<12>*>(sg.args), local); break;
-          case 24: vec_tile<24>(*static_cast<const VecJobArgs<24>*>(sg.args), local); break;
         }
       }
     }
@@ -149,7 +158,9 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __re
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(&ctr[1 + sg.done_id], 1u);
+      wait_deps(b ^ 1);
     }
+    __syncthreads();
   }
 }
 
@@ -157,10 +168,13 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_kernel(const Seg* __re
 
 using namespace moma;
 
-// A 768-bit transform job of a batch, run with the per-call pass kernels after the
-// persistent launch (intermediates in the batch's scratch: [s1 | s2 | fa | fb]).
+// A 768-bit job of a batch, run with the per-call kernels after the persistent launch
+// (transform intermediates in the batch's scratch: [s1 | s2 | fa | fb]; vector ops keep a copy
+// of the axpy scalar).
 struct BatchDeferred {
   int op = 0;
+  size_t n = 0;
+  std::vector<uint32_t> alpha;
   moma_ctx* ctx = nullptr;
   const moma::Plan* fwd = nullptr;
   const moma::Plan* inv = nullptr;
@@ -183,6 +197,7 @@ struct moma_batch {
   int grid = 0;
   uint64_t wait_polls = kDefaultWaitPolls;
   Seg* d_segs = nullptr;
+  uint32_t* d_tile_seg = nullptr;  // segment index of every tile
   uint8_t* d_args = nullptr;
   uint32_t* d_ctr = nullptr;
   int* d_status = nullptr;
@@ -388,9 +403,11 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     const uint32_t no_id[2] = {0, 0}, no_cnt[2] = {0, 0};
     uint32_t* base = b->d_scratch + scratch_off[j];
     const size_t w = (size_t)ctx->L * jb.n;
-    if (jb.op <= MOMA_OP_POLYMUL && ctx->L > 12) {
+    if (ctx->L > 12) {  // 768-bit jobs: per-call kernels after the persistent launch
       BatchDeferred d;
       d.op = jb.op;
+      d.n = jb.n;
+      if (jb.op == MOMA_OP_AXPY) d.alpha.assign(jb.alpha, jb.alpha + ctx->L);
       d.ctx = ctx;
       d.fwd = fwd[j];
       d.inv = inv[j];
@@ -399,7 +416,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
       d.out = jb.out;
       d.scratch = base;
       d.w = w;
-      d.cfg = ntt_config(ctx, jb.op, log2_n(jb.n));
+      if (jb.op <= MOMA_OP_POLYMUL) d.cfg = ntt_config(ctx, jb.op, log2_n(jb.n));
       b->deferred.push_back(d);
     } else if (jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV) {
       const Plan* pl = jb.op == MOMA_OP_NTT_FWD ? fwd[j] : inv[j];
@@ -466,6 +483,16 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     return MOMA_ERR_SIZE;
   }
   b->total = (uint32_t)total;
+  std::vector<uint32_t> tile_seg((size_t)total);
+  for (size_t si = 0; si < b->segs.size(); ++si)
+    std::fill(tile_seg.begin() + b->segs[si].first, tile_seg.begin() + b->segs[si].first + b->segs[si].ntiles,
+              (uint32_t)si);
+  if (cudaMallocAsync(&b->d_tile_seg, std::max<size_t>(tile_seg.size(), 1) * 4, ss) != cudaSuccess ||
+      (total && cudaMemcpyAsync(b->d_tile_seg, tile_seg.data(), tile_seg.size() * 4, cudaMemcpyHostToDevice, ss) !=
+                    cudaSuccess)) {
+    moma_batch_destroy(b);
+    return MOMA_ERR_OOM;
+  }
   b->ncounters = counter;
   if (cudaMemcpyAsync(b->d_args, ab.bytes.data(), ab.bytes.size(), cudaMemcpyHostToDevice, ss) != cudaSuccess ||
       cudaMemcpyAsync(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ss) !=
@@ -499,8 +526,8 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
 static moma_status batch_launch(moma_batch* b, cudaStream_t st) {
   if (b->total > 0) {
     if (cudaMemsetAsync(b->d_ctr, 0, (1 + b->ncounters) * sizeof(uint32_t), st) != cudaSuccess) return MOMA_ERR_CUDA;
-    batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_segs, (uint32_t)b->segs.size(), b->total, b->d_ctr,
-                                                          b->d_status, b->wait_polls);
+    batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_segs, b->d_tile_seg, b->total, b->d_ctr, b->d_status,
+                                                          b->wait_polls);
     const moma_status rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
   }
@@ -512,6 +539,8 @@ static moma_status batch_launch(moma_batch* b, cudaStream_t st) {
       rc = run_plan_buffers(d.ctx, d.fwd, 1, d.a, nullptr, d.out, d.cfg, s1, s2, st);
     } else if (d.op == MOMA_OP_NTT_INV) {
       rc = run_plan_buffers(d.ctx, d.inv, 1, d.a, nullptr, d.out, d.cfg, s1, s2, st);
+    } else if (d.op >= MOMA_OP_ADD) {
+      rc = launch_vec(d.ctx, d.op - MOMA_OP_ADD, d.n, d.a, d.b, d.out, d.alpha.empty() ? nullptr : d.alpha.data(), st);
     } else {
       uint32_t* fa = d.scratch + 2 * d.w;
       uint32_t* fb = d.scratch + 3 * d.w;
@@ -591,7 +620,8 @@ extern "C" void moma_batch_destroy(moma_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   cudaStream_t ss = setup_stream(b->device);
-  for (void* p : {(void*)b->d_segs, (void*)b->d_args, (void*)b->d_ctr, (void*)b->d_status, (void*)b->d_scratch})
+  for (void* p : {(void*)b->d_segs, (void*)b->d_tile_seg, (void*)b->d_args, (void*)b->d_ctr, (void*)b->d_status,
+                  (void*)b->d_scratch})
     if (p) cudaFreeAsync(p, ss);
   delete b;
 }

@@ -88,7 +88,7 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
 // for 64 registers up to 256 bits and 102 at 384 bits, without spills, for more resident CTAs.
 template <int L, bool WIDE, bool TIGHT>
 __global__ void __launch_bounds__(TIGHT ? 128 : kNttMaxThreads,
-                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 1)) : (L <= 12 ? 3 : 1))
+                                  TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 3)) : (L <= 12 ? 3 : 1))
     ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ __align__(16) uint32_t sm[];
   ntt_tile<L, WIDE>(p, blockIdx.x, sm);
@@ -414,7 +414,7 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
   }
   const bool wide = cfg.engine == 2;
   const int th = cfg.cta_threads;
-  const bool tight = cfg.tight_regs != 0 && th <= 128 && ctx->L <= 12;
+  const bool tight = cfg.tight_regs != 0 && th <= 128;
 #define MOMA_RUN_PASS(LL)                                                                              \
   return wide ? (tight ? run_pass<LL, true, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)   \
                        : run_pass<LL, true, false>(ctx, pl, d, count, src, src2, dst, flags, th, st)) \
@@ -425,6 +425,7 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
     case 8: MOMA_RUN_PASS(8)
     case 12: MOMA_RUN_PASS(12)
     case 24:
+      if (tight) return run_pass<24, false, true>(ctx, pl, d, count, src, src2, dst, flags, th, st);
       return wide ? run_pass<24, true, false>(ctx, pl, d, count, src, src2, dst, flags, th, st)
                   : run_pass<24, false, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   }
