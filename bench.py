@@ -558,9 +558,10 @@ def run_sensitivity(steps=5):
 
 def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
     """The served stream: Poisson arrivals of n_jobs transforms (2^12..2^22) and mulmod/axpy
-    vectors (2^16..2^24) at 256/384/768 bits, continuous batching under a 40 GB budget.
-    Capacity is measured closed-loop (all requests present at t = 0); the open-loop run offers
-    load x capacity."""
+    vectors (2^16..2^24) at 256/384/768 bits, continuous batching under a 40 GB budget, with
+    size-class micro-batches (serve.Scheduler policy "class").  Capacity is measured closed-loop
+    (all requests present at t = 0); the open-loop run offers load x capacity.  The same open-loop
+    stream under plain FIFO micro-batches is reported beside it."""
     import torch
 
     from paper_2501_07535_gb300 import batch, serve
@@ -569,15 +570,17 @@ def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
     ex = serve.GpuExecutor(ctxs, slots=slots)
     try:
         ex.prewarm(jobs)
-        closed = serve.serve([0.0] * n_jobs, jobs, ctxs, slots=slots, executor=ex).summary()
+        closed = serve.serve([0.0] * n_jobs, jobs, ctxs, slots=slots, executor=ex, policy="class").summary()
         capacity = closed["jobs_per_s"]
         rate = load * capacity
         arrivals = [a / rate for a in unit_arrivals]
-        opened = serve.serve(arrivals, jobs, ctxs, slots=slots, executor=ex).summary()
+        opened = serve.serve(arrivals, jobs, ctxs, slots=slots, executor=ex, policy="class").summary()
+        fifo = serve.serve(arrivals, jobs, ctxs, slots=slots, executor=ex, policy="fifo").summary()
         torch.cuda.synchronize()
-        return {"jobs": n_jobs, "capacity_jobs_per_s": capacity, "offered_load": load,
+        return {"jobs": n_jobs, "policy": "class", "capacity_jobs_per_s": capacity, "offered_load": load,
                 "offered_jobs_per_s": round(rate, 1), "closed_loop": closed, "open_loop": opened,
-                "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"], "budget_gb": 40, "slots": slots}
+                "open_loop_fifo": fifo, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"], "budget_gb": 40,
+                "slots": slots}
     finally:
         ctxs.close()
 

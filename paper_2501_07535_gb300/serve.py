@@ -58,16 +58,67 @@ class ServeStats:
 
 
 class Scheduler:
-    """Admission by memory budget, a fixed number of concurrent micro-batches, FIFO order."""
+    """Admission by memory budget, a fixed number of concurrent micro-batches.
+
+    policy "fifo": a micro-batch takes jobs from the head of the queue in arrival order.
+    policy "class": the head of the queue opens the micro-batch and fixes its size class (small or
+    large by the executor's cost estimate); the batch then takes, in arrival order from the first
+    `lookahead` queued jobs, only jobs of the same class, up to `cost_cap` of estimated work (or the
+    head's own cost, if larger).  A micro-batch completes as a whole, so this keeps small jobs from
+    waiting for a large one launched with them; the head of the queue is always served next, so no
+    job waits behind later arrivals of its own class.
+    """
 
     def __init__(self, executor, budget_bytes: int = BUDGET_BYTES, slots: int = 4, max_batch_jobs: int = 64,
-                 clock=time.perf_counter, idle_sleep_s: float = 20e-6):
+                 clock=time.perf_counter, idle_sleep_s: float = 20e-6, policy: str = "fifo",
+                 large_cost: float = 5e-4, cost_cap: float = 2e-3, lookahead: int = 512):
+        if policy not in ("fifo", "class"):
+            raise ValueError("policy must be 'fifo' or 'class'")
         self.ex = executor
         self.budget = budget_bytes
         self.slots = slots
         self.max_batch = max_batch_jobs
         self.clock = clock
         self.idle_sleep = idle_sleep_s
+        self.policy = policy
+        self.large_cost = large_cost
+        self.cost_cap = cost_cap
+        self.lookahead = lookahead
+
+    def _cost(self, job) -> float:
+        f = getattr(self.ex, "cost", None)
+        return f(job) if f else 0.0
+
+    def _take_class(self, queue, jobs, used, rejected):
+        """One size-homogeneous micro-batch from the queue (policy "class")."""
+        batch, nbytes, cost = [], 0, 0.0
+        skipped = []
+        cls = None
+        cap = self.cost_cap
+        scanned = 0
+        while queue and len(batch) < self.max_batch and scanned < self.lookahead:
+            j = queue.popleft()
+            scanned += 1
+            need = self.ex.footprint(jobs[j])
+            if need > self.budget:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+                rejected.append(j)
+                continue
+            c = self._cost(jobs[j])
+            large = c >= self.large_cost
+            if cls is None:  # the head of the queue opens the batch
+                if used + need > self.budget:
+                    skipped.append(j)
+                    break
+                cls = large
+                cap = max(cap, c)
+            elif large != cls or cost + c > cap or used + nbytes + need > self.budget:
+                skipped.append(j)
+                continue
+            batch.append(j)
+            nbytes += need
+            cost += c
+        queue.extendleft(reversed(skipped))  # untaken jobs keep their order at the front
+        return batch, nbytes
 
     def run(self, arrivals, jobs) -> ServeStats:
         n = len(jobs)
@@ -99,19 +150,22 @@ class Scheduler:
                 progressed = True
             inflight = keep
             while queue and len(inflight) < self.slots:
-                batch, nbytes = [], 0
-                while queue and len(batch) < self.max_batch:
-                    j = queue[0]
-                    need = self.ex.footprint(jobs[j])
-                    if need > self.budget:  # can never fit: refuse it (MOMA_ERR_BUDGET)
-                        rejected.append(j)
+                if self.policy == "class":
+                    batch, nbytes = self._take_class(queue, jobs, used, rejected)
+                else:
+                    batch, nbytes = [], 0
+                    while queue and len(batch) < self.max_batch:
+                        j = queue[0]
+                        need = self.ex.footprint(jobs[j])
+                        if need > self.budget:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+                            rejected.append(j)
+                            queue.popleft()
+                            continue
+                        if used + nbytes + need > self.budget:
+                            break
+                        batch.append(j)
+                        nbytes += need
                         queue.popleft()
-                        continue
-                    if used + nbytes + need > self.budget:
-                        break
-                    batch.append(j)
-                    nbytes += need
-                    queue.popleft()
                 if not batch:
                     break
                 handle = self.ex.launch([jobs[j] for j in batch])
@@ -176,6 +230,16 @@ class GpuExecutor:
                 t = m.repeat(1, job.n // N).contiguous()
             self._inputs[key] = t
         return t
+
+    def cost(self, job) -> float:
+        """Rough GPU seconds of one job (scheduling only): transforms scale as n log2 n L^2 from a
+        256-bit 2^20-point transform of ~0.25 ms, vector products as n L^2 from ~0.45 ms per 2^24
+        256-bit elements (additions are cheaper; they are rated like products)."""
+        r = (job.width / 256) ** 2
+        if job.op in ("ntt_fwd", "ntt_inv", "polymul"):
+            lg = max(1, int(job.n).bit_length() - 1)
+            return 0.25e-3 * r * job.n * lg / (20 << 20) * (3 if job.op == "polymul" else 1)
+        return 0.45e-3 * r * job.n / (1 << 24)
 
     def footprint(self, job) -> int:
         L = job.width // 32
@@ -246,7 +310,8 @@ def served_jobs(n_jobs=10000, seed=0, rate_per_s=1000.0):
     return inputs.served_stream(n_jobs=n_jobs, seed=seed, rate_per_s=rate_per_s)
 
 
-def serve(arrivals, jobs, contexts, slots=4, budget_bytes=BUDGET_BYTES, max_batch_jobs=64, executor=None):
+def serve(arrivals, jobs, contexts, slots=4, budget_bytes=BUDGET_BYTES, max_batch_jobs=64, executor=None,
+          policy="fifo"):
     ex = executor or GpuExecutor(contexts, slots=slots)
-    sched = Scheduler(ex, budget_bytes=budget_bytes, slots=slots, max_batch_jobs=max_batch_jobs)
+    sched = Scheduler(ex, budget_bytes=budget_bytes, slots=slots, max_batch_jobs=max_batch_jobs, policy=policy)
     return sched.run(arrivals, jobs)

@@ -80,3 +80,58 @@ def test_served_stream_shape():
             assert j.width in (256, 384, 768) and 1 << 12 <= j.n <= 1 << 22
         else:
             assert j.op in ("mul", "axpy") and 1 << 16 <= j.n <= 1 << 24
+
+
+class CostExecutor(FakeExecutor):
+    """A batch takes the sum of its jobs' costs (job.n microseconds)."""
+
+    def cost(self, job):
+        return job.n * 1e-6
+
+    def launch(self, jobs):
+        now = time.perf_counter() - self.t0
+        done = now + sum(self.cost(j) for j in jobs)
+        self.launches.append((now, done, [j.seed for j in jobs]))
+        return done
+
+
+def _mixed(n, seed=3):
+    import random
+    rng = random.Random(seed)
+    # 1 in 8 jobs is large (3 ms), the rest small (0.05 ms)
+    return [inputs.Job(op="mul", width=256, n=3000 if rng.random() < 0.125 else 50, seed=i) for i in range(n)]
+
+
+def _small_latencies(st, jobs):
+    lat = st.latencies_s
+    return sorted(lat[i] for i, j in enumerate(jobs) if j.n == 50)
+
+
+def test_class_policy_keeps_small_jobs_out_of_large_batches():
+    jobs = _mixed(400)
+    arrivals = [i * 1.2e-4 for i in range(len(jobs))]
+    ex = CostExecutor(footprint=lambda j: 1)
+    st = serve.Scheduler(ex, budget_bytes=10**9, slots=4, max_batch_jobs=32, policy="class",
+                         large_cost=5e-4, cost_cap=1e-3).run(arrivals, jobs)
+    assert st.completed == len(jobs) and st.rejected == 0
+    for _, _, seeds in ex.launches:  # every micro-batch is one size class
+        assert len({jobs[s].n for s in seeds}) == 1
+    # the head of the queue opens each batch: batch heads leave in arrival order
+    heads = [seeds[0] for _, _, seeds in ex.launches]
+    assert heads == sorted(heads)
+    fifo_ex = CostExecutor(footprint=lambda j: 1)
+    fifo = serve.Scheduler(fifo_ex, budget_bytes=10**9, slots=4, max_batch_jobs=32).run(arrivals, jobs)
+    cls_small, fifo_small = _small_latencies(st, jobs), _small_latencies(fifo, jobs)
+    q = int(0.9 * len(cls_small))
+    assert cls_small[q] < fifo_small[q]  # small jobs no longer wait for a large one in their batch
+
+
+def test_class_policy_respects_budget_and_rejects_oversize():
+    jobs = _mixed(120) + [inputs.Job(op="mul", width=256, n=10**7, seed=999)]
+    arrivals = [0.0] * len(jobs)
+    ex = CostExecutor(footprint=lambda j: j.n)
+    sched = serve.Scheduler(ex, budget_bytes=7000, slots=4, max_batch_jobs=64, policy="class")
+    st = sched.run(arrivals, jobs)
+    assert st.rejected == 1 and sched.rejected == [120]
+    assert st.completed == 120
+    assert st.max_inflight_bytes <= 7000
