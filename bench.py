@@ -53,10 +53,6 @@ def word_products_per_mulmod(L):
     return 2 * L * L + L
 
 
-def imad_per_mulmod(L):
-    return 2 * word_products_per_mulmod(L)  # a word product is a lo and a hi multiply-add
-
-
 # ----------------------------------------------------------------------------- CPU oracle
 
 def _oracle_ntt_worker(args):

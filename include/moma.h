@@ -80,9 +80,9 @@ moma_status moma_ctx_create(const uint32_t *q, int bits, moma_ctx **out);
  * word.  Inputs and outputs are canonical residues as for moma_ctx_create (no Montgomery form
  * visible to the caller: mulmod is two Montgomery products, the second by R^2 mod q;
  * twiddles, the axpy scalar and n^-1 are kept in Montgomery form internally).
- * Supported: moma_vec_*, moma_ntt_fwd/inv, moma_ntt_{fwd,inv}_many, moma_polymul,
- * moma_ntt_fwd_noalloc, moma_ctx_root, configuration and autotuning (the product engine
- * setting is ignored).  Negacyclic calls and batch jobs give MOMA_ERR_UNSUPPORTED. */
+ * Every call accepts such a context; the product engine setting is ignored (Montgomery
+ * products are carry chains).  In batches their jobs run with the per-call kernels after the
+ * persistent launch, like 768-bit jobs. */
 moma_status moma_ctx_create_full(const uint32_t *q, int bits, moma_ctx **out);
 
 /* 1 for a context made by moma_ctx_create_full, else 0 (also for NULL). */
@@ -197,9 +197,9 @@ moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, ui
  * (out = a * b mod (x^n - 1, q)), MOMA_OP_ADD / SUB / MUL (out = a op b), MOMA_OP_AXPY
  * (out = alpha * a + b, alpha a HOST array of L limbs).  Device vectors follow the
  * conventions above; each job uses its own context (any widths and moduli may be mixed).
- * Jobs at 128 to 384 bits are tiles of the persistent launch; 768-bit jobs run with the
- * per-call kernels right after it, on the same stream (and in the same CUDA graph).
- * Contexts made by moma_ctx_create_full are refused (MOMA_ERR_UNSUPPORTED). */
+ * Jobs at 128 to 384 bits are tiles of the persistent launch; 768-bit jobs and jobs of
+ * full-width contexts (moma_ctx_create_full) run with the per-call kernels right after it, on
+ * the same stream (and in the same CUDA graph). */
 typedef struct {
   int op;
   moma_ctx *ctx;

@@ -15,9 +15,10 @@
 //
 // Widths are mixed inside one launch: the CTA dispatches on the tile's limb count.  Products
 // use whole mad.wide rows up to 256 bits and carry chains at 384 bits (the faster form of each
-// width on GB300); results are identical either way.  768-bit jobs are not tiles of the
-// persistent kernel (their registers would cut the occupancy of every other tile): they run with
-// the per-call kernels right after it, on the same stream and inside the same CUDA graph.
+// width on GB300); results are identical either way.  768-bit jobs and jobs over full-width moduli
+// (Montgomery arithmetic) are not tiles of the persistent kernel (their registers and code would
+// cut the occupancy of every other tile): they run with the per-call kernels right after it, on
+// the same stream and inside the same CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -344,7 +345,6 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     moma_ctx* ctx = jb.ctx;
     if (!ctx || !jb.a || !jb.out) return MOMA_ERR_INVALID_ARG;
     if (ctx->device != dev) return MOMA_ERR_INVALID_ARG;
-    if (ctx->mont) return MOMA_ERR_UNSUPPORTED;  // full-width moduli: per-call API only
     const bool ntt = jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV || jb.op == MOMA_OP_POLYMUL;
     if (!ntt && (jb.op < MOMA_OP_ADD || jb.op > MOMA_OP_AXPY)) return MOMA_ERR_INVALID_ARG;
     if ((jb.op == MOMA_OP_POLYMUL || (!ntt)) && !jb.b) return MOMA_ERR_INVALID_ARG;
@@ -358,9 +358,10 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     const int lg = log2_n(jb.n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
     moma_config cfg = ntt_config(ctx, jb.op, lg);
-    // 768-bit transforms keep their per-call schedule (they run as per-pass launches)
-    const int tl = ctx->L > 12 ? cfg.tile_log : std::min(cfg.tile_log, kBatchTileLog);
-    const int rmax = ctx->L > 12 ? cfg.max_logr : std::min(cfg.max_logr, tl);
+    // jobs run with the per-call kernels (768 bits, full-width moduli) keep their per-call schedule
+    const bool per_call = ctx->L > 12 || ctx->mont;
+    const int tl = per_call ? cfg.tile_log : std::min(cfg.tile_log, kBatchTileLog);
+    const int rmax = per_call ? cfg.max_logr : std::min(cfg.max_logr, tl);
     Plan* pl = nullptr;
     moma_status rc;
     if (jb.op != MOMA_OP_NTT_INV) {
@@ -403,7 +404,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     const uint32_t no_id[2] = {0, 0}, no_cnt[2] = {0, 0};
     uint32_t* base = b->d_scratch + scratch_off[j];
     const size_t w = (size_t)ctx->L * jb.n;
-    if (ctx->L > 12) {  // 768-bit jobs: per-call kernels after the persistent launch
+    if (ctx->L > 12 || ctx->mont) {  // 768-bit jobs, full-width moduli: per-call kernels afterwards
       BatchDeferred d;
       d.op = jb.op;
       d.n = jb.n;
@@ -504,7 +505,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
   // shared memory: the largest transform tile of the batch
   size_t smem = 0;
   for (int j = 0; j < njobs; ++j)
-    if (jobs[j].op <= MOMA_OP_POLYMUL && jobs[j].ctx->L <= 12)
+    if (jobs[j].op <= MOMA_OP_POLYMUL && jobs[j].ctx->L <= 12 && !jobs[j].ctx->mont)
       smem = std::max(smem, (size_t)jobs[j].ctx->L * 4u << kBatchTileLog);
   b->smem = smem;
   if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(12 * 4 << kBatchTileLog)) !=

@@ -343,7 +343,6 @@ moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int ma
   if (st) return st;
   if (logn > ctx->two_adicity || logn < 1 || logn > kMaxLogN) return MOMA_ERR_SIZE;
   if (nega && logn + 1 > ctx->two_adicity) return MOMA_ERR_SIZE;  // needs a 2n-th root
-  if (nega && ctx->mont) return MOMA_ERR_UNSUPPORTED;
   if (logn <= tile_log) max_logr = 0;  // single pass: the split does not matter
   std::lock_guard<std::mutex> g(ctx->lock);
   auto key = std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr, nega ? 1 : 0);

@@ -139,7 +139,7 @@ def test_full_width_polymul_and_many(gpu, fctx, width, lg):
         assert inputs.to_ints(gpu.to_host(dy[t])) == oracle.ntt_fwd(inputs.to_ints(xs[t]), q)
 
 
-def test_full_width_noalloc_and_refusals(gpu, fctx):
+def test_full_width_noalloc(gpu, fctx):
     q = inputs.prime_full(256).q
     h = fctx[256]
     n = 1 << 12
@@ -149,12 +149,73 @@ def test_full_width_noalloc_and_refusals(gpu, fctx):
     gpu.moma_ntt_fwd_noalloc(h, n, x, got)
     torch.cuda.synchronize()
     assert torch.equal(want, got)
-    with pytest.raises(gpu.MomaError) as ei:
-        gpu.moma_ntt_fwd_negacyclic(h, n, x, got)
-    assert ei.value.code == 9
-    with pytest.raises(gpu.MomaError) as ei:
-        gpu.moma_batch_create([{"op": "ntt_fwd", "ctx": h, "n": n, "a": x, "out": got}])
-    assert ei.value.code == 9
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("lg", [1, 6, 11])
+def test_full_width_negacyclic(gpu, fctx, width, lg):
+    """psi tables in Montgomery form; forward = evaluation at the odd powers of psi."""
+    q = inputs.prime_full(width).q
+    L = width // 32
+    n = 1 << lg
+    h = fctx[width]
+    a = inputs.residues(q, L, n, 70 + lg)
+    b = inputs.residues(q, L, n, 80 + lg)
+    ai, bi = inputs.to_ints(a), inputs.to_ints(b)
+    da, db = gpu.to_device(a), gpu.to_device(b)
+    fa, back, prod = torch.empty_like(da), torch.empty_like(da), torch.empty_like(da)
+    gpu.moma_ntt_fwd_negacyclic(h, n, da, fa)
+    gpu.moma_ntt_inv_negacyclic(h, n, fa, back)
+    gpu.moma_polymul_negacyclic(h, n, da, db, prod)
+    torch.cuda.synchronize()
+    assert inputs.to_ints(gpu.to_host(fa)) == oracle.ntt_fwd_negacyclic(ai, q)
+    assert torch.equal(back, da)
+    assert inputs.to_ints(gpu.to_host(prod)) == oracle.negacyclic_convolution_naive(ai, bi, q)
+
+
+def test_full_width_batch_jobs(gpu):
+    """Full-width jobs in a batch (per-call kernels after the persistent launch) next to Barrett jobs;
+    direct run, then graph capture and replay, against the oracle."""
+    from paper_2501_07535_gb300 import moma
+    specs = [("ntt_fwd", 256, 1 << 10, True), ("polymul", 384, 1 << 9, True), ("mul", 768, 3001, True),
+             ("axpy", 128, 4096, True), ("ntt_inv", 256, 1 << 11, False), ("add", 256, 999, True)]
+    hs, dev, host, alphas = [], [], [], []
+    try:
+        for i, (op, w, n, full) in enumerate(specs):
+            q = inputs.prime_full(w).q if full else inputs.prime(w).q
+            h = gpu.moma_ctx_create_full(q, w) if full else gpu.moma_ctx_create(q, w)
+            hs.append(h)
+            a = inputs.residues(q, w // 32, n, 300 + i)
+            b = inputs.residues(q, w // 32, n, 400 + i)
+            host.append((q, a, b))
+            dev.append((gpu.to_device(a), gpu.to_device(b), torch.empty((w // 32, n), dtype=torch.int32,
+                                                                        device="cuda")))
+            alphas.append(inputs.scalar_residue(q, 500 + i) if op == "axpy" else None)
+        jobs = [{"op": op, "ctx": hs[i], "n": n, "a": dev[i][0], "b": dev[i][1], "out": dev[i][2],
+                 "alpha": alphas[i]} for i, (op, w, n, full) in enumerate(specs)]
+        bh = moma.moma_batch_create(jobs)
+        s = torch.cuda.Stream()
+        try:
+            with torch.cuda.stream(s):
+                for _ in range(3):
+                    for d in dev:
+                        d[2].zero_()
+                    moma.moma_batch_run(bh, s)
+            s.synchronize()
+            assert moma.moma_batch_sync_status(bh) == 0
+        finally:
+            moma.moma_batch_destroy(bh)
+        for i, (op, w, n, full) in enumerate(specs):
+            q, a, b = host[i]
+            ai, bi = inputs.to_ints(a), inputs.to_ints(b)
+            want = {"ntt_fwd": lambda: oracle.ntt_fwd(ai, q), "ntt_inv": lambda: oracle.ntt_inv(ai, q),
+                    "polymul": lambda: oracle.polymul_cyclic(ai, bi, q), "mul": lambda: oracle.vec_mulmod(ai, bi, q),
+                    "add": lambda: oracle.vec_addmod(ai, bi, q),
+                    "axpy": lambda: oracle.vec_axpy(alphas[i], ai, bi, q)}[op]()
+            assert inputs.to_ints(gpu.to_host(dev[i][2])) == want, (op, w, full)
+    finally:
+        for h in hs:
+            gpu.moma_ctx_destroy(h)
 
 
 def test_full_width_autotune(gpu, fctx):

@@ -8,7 +8,8 @@ from paper_2501_07535_gb300 import batch, inputs, moma, serve
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone(gpu):
+@pytest.mark.parametrize("policy", ["fifo", "class"])
+def test_served_results_equal_alone(gpu, policy):
     arrivals, jobs = inputs.served_stream(n_jobs=160, seed=3, rate_per_s=20000.0, ntt_log_range=(6, 12),
                                           vec_log_range=(8, 14))
     assert any(j.width == 768 and j.op.startswith("ntt") for j in jobs)
@@ -16,7 +17,7 @@ def test_served_results_equal_alone(gpu):
     ex = serve.GpuExecutor(ctxs, slots=4, keep_outputs=True, master_log=12)
     try:
         ex.prewarm(jobs)
-        st = serve.serve(arrivals, jobs, ctxs, slots=4, max_batch_jobs=16, executor=ex)
+        st = serve.serve(arrivals, jobs, ctxs, slots=4, max_batch_jobs=16, executor=ex, policy=policy)
         torch.cuda.synchronize()
         assert st.completed == len(jobs) and st.rejected == 0
         assert st.max_concurrent_batches >= 1
