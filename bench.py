@@ -573,7 +573,10 @@ def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
         opened = serve.serve(arrivals, jobs, ctxs, slots=slots, executor=ex, policy="class").summary()
         fifo = serve.serve(arrivals, jobs, ctxs, slots=slots, executor=ex, policy="fifo").summary()
         torch.cuda.synchronize()
-        return {"jobs": n_jobs, "policy": "class", "capacity_jobs_per_s": capacity, "offered_load": load,
+        plain_s = serve.run_plain(jobs, ex)
+        return {"jobs": n_jobs, "policy": "class", "capacity_jobs_per_s": capacity,
+                "plain_per_call_jobs_per_s": round(n_jobs / plain_s, 1),
+                "served_over_plain": round(capacity / (n_jobs / plain_s), 3), "offered_load": load,
                 "offered_jobs_per_s": round(rate, 1), "closed_loop": closed, "open_loop": opened,
                 "open_loop_fifo": fifo, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"], "budget_gb": 40,
                 "slots": slots}

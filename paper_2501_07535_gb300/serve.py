@@ -304,6 +304,40 @@ class GpuExecutor:
         return self.t_base + self.base.elapsed_time(handle["event"]) * 1e-3
 
 
+def run_plain(jobs, executor, stream=None):
+    """The same jobs as plain per-call launches (one library call per job, arrival order, one
+    stream, all present at t = 0), on the executor's resident operands.  Returns the seconds from
+    the first launch to the end of the last job (CUDA events)."""
+    import torch
+
+    from . import moma
+    ctx = executor.ctx
+    outs = {}
+    st = stream or torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for j in jobs:
+            a = executor.operand(j, 0)
+            key = (j.width, j.n)
+            if key not in outs:
+                outs[key] = torch.empty_like(a)
+            o = outs[key]
+            c = ctx.get(j.width, j.prime_seed)
+            if j.op == "ntt_fwd":
+                moma.moma_ntt_fwd(c, j.n, a, o, st)
+            elif j.op == "ntt_inv":
+                moma.moma_ntt_inv(c, j.n, a, o, st)
+            elif j.op == "mul":
+                moma.moma_vec_mulmod(c, j.n, a, executor.operand(j, 1), o, st)
+            else:
+                al = inputs.scalar_residue(inputs.prime(j.width, j.prime_seed).q, j.seed)
+                moma.moma_vec_axpymod(c, j.n, al, a, executor.operand(j, 1), o, st)
+        e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
 def served_jobs(n_jobs=10000, seed=0, rate_per_s=1000.0):
     """The served stream: transforms (2^12..2^22) and mulmod/axpy vectors (2^16..2^24) at
     256/384/768 bits, Poisson arrivals."""
