@@ -33,6 +33,7 @@
 namespace moma {
 
 constexpr int kBatchThreads = 128;
+constexpr int kBatchMinBlocks = 5;      // register cap 102: five CTAs per SM where shared memory allows
 constexpr int kBatchTileLog = 10;       // transform tiles of 2^10 elements
 constexpr uint32_t kVecTile = 2048;     // elements per vector-op tile
 constexpr uint64_t kDefaultWaitPolls = 1ull << 24;
@@ -92,15 +93,12 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   return v;
 }
 
-#ifndef MOMA_BATCH_MINB
-#define MOMA_BATCH_MINB 5
-#endif
 // A CTA claims its next tile (one atomic, one look-up in the tile -> segment table) while it
 // works on the current one, and waits for the next tile's dependencies right after publishing
 // the current one.  Shared state is double-buffered by iteration parity.  Progress: the lowest
 // unfinished tile depends only on finished tiles, and whichever resident CTA holds it (as its
 // current or its claimed next tile) reaches it, so every wait ends.
-__global__ void __launch_bounds__(kBatchThreads, MOMA_BATCH_MINB)
+__global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks)
     batch_kernel(const Seg* __restrict__ segs, const uint32_t* __restrict__ tile_seg, uint32_t total, uint32_t* ctr,
                  int* status, uint64_t wait_polls) {
   extern __shared__ __align__(16) uint32_t sm[];
