@@ -407,15 +407,17 @@ def run_profile(args):
     """Small cases for ncu captures (each op: one untimed call first, then `steps` calls):
     ntt: batched forward 256-bit 2^20 NTTs; mul / add / axpy: the 2^24-element 256-bit vector op;
     ntt768: 768-bit 2^16 NTTs (batch 8); mont_ntt / mont_mul: the 256-bit NTT and mulmod over a
-    full-width modulus; batch: the uneven batch at reduced sizes (2^10..2^16, 64 jobs)."""
+    full-width modulus; batch: the uneven batch at reduced sizes (2^10..2^16, 64 jobs); batch_large:
+    128 jobs of the uneven mix at its full size range (2^10..2^20)."""
     import numpy as np
     import torch
 
     from paper_2501_07535_gb300 import batch, build, inputs, moma
     build.build()
     op = args.profile_op
-    if op == "batch":
-        jobs = inputs.uneven_batch(n_jobs=64, seed=0, log_n_range=(10, 16))
+    if op in ("batch", "batch_large"):
+        nj, lr = (64, (10, 16)) if op == "batch" else (128, (10, 20))
+        jobs = inputs.uneven_batch(n_jobs=nj, seed=0, log_n_range=lr)
         js = batch.JobSet(jobs)
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
@@ -425,7 +427,7 @@ def run_profile(args):
         status = js.status()
         js.close()
         js.ctx.close()
-        print(json.dumps({"profile": "batch", "jobs": 64, "calls": 1 + args.steps, "status": status}))
+        print(json.dumps({"profile": op, "jobs": nj, "calls": 1 + args.steps, "status": status}))
         return
     full = op.startswith("mont_")
     width = 768 if op == "ntt768" else WIDTH
@@ -661,7 +663,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small NTT-only case for ncu captures")
     ap.add_argument("--ntt-batch", type=int, default=8)
     ap.add_argument("--profile-op", default="ntt",
-                    choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "batch"])
+                    choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "batch", "batch_large"])
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -275,8 +275,9 @@ typedef enum {
  *   cta_threads transforms: threads per CTA (32, 64, 128 or 256).  Each CTA owns one tile;
  *              small CTAs synchronise fewer warps between butterfly stages.
  *   tight_regs transforms: 1 = kernels compiled for fewer registers per thread (64 up to 256
- *              bits, 102 at 384 bits) so that more CTAs of at most 128 threads are resident;
- *              0 = default. */
+ *              bits, 102 at 384 bits, 170 at 768 bits) so that more CTAs of at most 128
+ *              threads are resident; 0 = no cap beyond the default (85 up to 384 bits).  The
+ *              default schedule sets 1 at 384 bits.  Ignored by full-width contexts. */
 typedef struct {
   int engine;
   int tile_log;
