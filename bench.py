@@ -518,8 +518,9 @@ def run_uneven_batch(steps, warmup, n_jobs=256, seed=0):
 
 
 def run_sensitivity(steps=5):
-    """Sec. 5.4 analogues: (1) forward NTT runtime against width at n = 4096 (batches of 256,
-    ns per butterfly = 2t/(n log2 n) as in Sec. 5.3); (2) mulmod with schoolbook carry chains,
+    """Sec. 5.4 analogues: (1) forward NTT runtime against width at n = 4096 from 64 to 1024 bits
+    (batches of 256, ns per butterfly = 2t/(n log2 n) as in Sec. 5.3), with the slowdown per
+    doubling of the width as the paper reports it; (2) mulmod with schoolbook carry chains,
     whole mad.wide products and Karatsuba (Eq. mulk) at each width, 2^22 elements; (3) the same
     mulmod and transform over a full-width modulus (Montgomery products, Sec. 5.2)."""
     import torch
@@ -540,7 +541,7 @@ def run_sensitivity(steps=5):
         return a.elapsed_time(b) / steps
 
     prev = None
-    for w in (128, 256, 384, 768):
+    for w in (64, 128, 256, 384, 512, 768, 1024):
         p = inputs.prime(w)
         ctx = moma.moma_ctx_create(p.q, w)
         n, cnt = 4096, 256
@@ -579,6 +580,10 @@ def run_sensitivity(steps=5):
             "ntt_over_barrett_time": round(fms / ms, 3)})
         moma.moma_ctx_destroy(fctx)
         moma.moma_ctx_destroy(ctx)
+    # the paper's sweep doubles the width (Sec. 5.4): 64 -> 128 -> 256 -> 512 -> 1024 bits
+    by = {r["bits"]: r["ns_per_butterfly"] for r in out["ntt_n4096"]}
+    out["ntt_n4096_slowdown_per_doubling"] = {f"{w}->{2 * w}": round(by[2 * w] / by[w], 2)
+                                              for w in (64, 128, 256, 512)}
     return out
 
 

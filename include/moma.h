@@ -12,11 +12,12 @@
  *
  * Conventions shared by every call
  * --------------------------------
- * Widths.  bits in {128, 256, 384, 768}; L = bits/32 limbs of 32 bits.  The modulus
- *   q must be odd and have exactly bits-4 bits (Sec. 5.2: a (k-4)-bit modulus for a
+ * Widths.  bits in {128, 256, 384, 768} (the widths of the workloads), and 64, 512, 1024
+ *   (the ends of the paper's width sweep, Sec. 5.4); L = bits/32 limbs of 32 bits.  The
+ *   modulus q must be odd and have exactly bits-4 bits (Sec. 5.2: a (k-4)-bit modulus for a
  *   k-bit container, which the Barrett constants of Sec. 3.1 need); otherwise
  *   MOMA_ERR_MODULUS.  Every width is supported by every call, except moma_ntt_fwd_noalloc
- *   (128 to 384 bits).  Full-width moduli (up to all bits of the container) take
+ *   (64 to 384 bits).  Full-width moduli (up to all bits of the container) take
  *   moma_ctx_create_full (Montgomery reduction); see there for the calls they support.
  * Layout.  A vector of n residues is limb-major: uint32 v[L][n], limb 0 the least
  *   significant word of each residue (the paper writes words most significant first;
@@ -66,7 +67,7 @@ const char *moma_status_string(moma_status s);
 /* ------------------------------------------------------------------ contexts */
 
 /* Create a context for modulus q (host array of bits/32 limbs, least significant
- * first).  Precomputes the Barrett constant mu = floor(2^(2B+3)/q), B = bits-4
+ * first; bits one of the widths above, else MOMA_ERR_INVALID_ARG).  Precomputes the Barrett constant mu = floor(2^(2B+3)/q), B = bits-4
  * (Sec. 3.1, Eq. mu) and the other per-modulus constants, and uploads them.  Transform
  * plans (twiddle tables) are built lazily per size.  *out receives the context; it is
  * set to NULL on error.  Uses the current CUDA device. */
@@ -178,8 +179,8 @@ moma_status moma_polymul_negacyclic(moma_ctx *ctx, size_t n, const uint32_t *a, 
  * path that must not wait on an allocator).  The paper has no counterpart; this is an
  * interface convenience of this library.
  * Limits and conditions:
- *   - L*n <= 2^20 words (n <= 2^18 at 128 bits, 2^17 at 256, 2^16 at 384); larger n gives
- *     MOMA_ERR_SIZE.  768-bit contexts give MOMA_ERR_UNSUPPORTED.
+ *   - L*n <= 2^20 words (n <= 2^19 at 64 bits, 2^18 at 128, 2^17 at 256, 2^16 at 384); larger
+ *     n gives MOMA_ERR_SIZE.  Contexts of 512 bits and up give MOMA_ERR_UNSUPPORTED.
  *   - The size's twiddle tables must already exist: call moma_ntt_fwd once with this
  *     context and n beforehand (that call allocates); otherwise MOMA_ERR_INVALID_ARG.
  *   - The context's device must be current.  The first call on a device looks up the

@@ -33,7 +33,8 @@ static moma_status ctx_create(const uint32_t* q, int bits, bool mont, moma_ctx**
   if (!out) return MOMA_ERR_INVALID_ARG;
   *out = nullptr;
   if (!q) return MOMA_ERR_INVALID_ARG;
-  if (bits != 128 && bits != 256 && bits != 384 && bits != 768) return MOMA_ERR_INVALID_ARG;
+  if (bits != 64 && bits != 128 && bits != 256 && bits != 384 && bits != 512 && bits != 768 && bits != 1024)
+    return MOMA_ERR_INVALID_ARG;
   const int L = bits / 32;
   BigU Q = BigU::from_words(q, L);
   if (!Q.is_odd()) return MOMA_ERR_MODULUS;  // odd: needed by every reduction

@@ -15,10 +15,10 @@
 //
 // Widths are mixed inside one launch: the CTA dispatches on the tile's limb count.  Products
 // use whole mad.wide rows up to 256 bits and carry chains at 384 bits (the faster form of each
-// width on GB300); results are identical either way.  768-bit jobs and jobs over full-width moduli
-// (Montgomery arithmetic) are not tiles of the persistent kernel (their registers and code would
-// cut the occupancy of every other tile): they run with the per-call kernels right after it, on
-// the same stream and inside the same CUDA graph.
+// width on GB300); results are identical either way.  Jobs at 512 bits and up and jobs over
+// full-width moduli (Montgomery arithmetic) are not tiles of the persistent kernel (their registers
+// and code would cut the occupancy of every other tile), nor are 64-bit jobs: they run with the
+// per-call kernels right after it, on the same stream and inside the same CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -276,6 +276,10 @@ moma_status pass_args_l(const moma_ctx* ctx, const Plan* pl, size_t pass, const 
   return MOMA_ERR_UNSUPPORTED;
 }
 
+// Jobs the persistent kernel runs as tiles: Barrett contexts of 128, 256 and 384 bits.  The others
+// (64-bit containers, 512 bits and up, full-width moduli) run with the per-call kernels after it.
+bool batch_tile_kind(const moma_ctx* ctx) { return !ctx->mont && (ctx->L == 4 || ctx->L == 8 || ctx->L == 12); }
+
 int log2_n(size_t n) {
   if (n == 0 || (n & (n - 1))) return -1;
   int k = 0;
@@ -357,7 +361,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
     moma_config cfg = ntt_config(ctx, jb.op, lg);
     // jobs run with the per-call kernels (768 bits, full-width moduli) keep their per-call schedule
-    const bool per_call = ctx->L > 12 || ctx->mont;
+    const bool per_call = !batch_tile_kind(ctx);
     const int tl = per_call ? cfg.tile_log : std::min(cfg.tile_log, kBatchTileLog);
     const int rmax = per_call ? cfg.max_logr : std::min(cfg.max_logr, tl);
     Plan* pl = nullptr;
@@ -402,7 +406,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     const uint32_t no_id[2] = {0, 0}, no_cnt[2] = {0, 0};
     uint32_t* base = b->d_scratch + scratch_off[j];
     const size_t w = (size_t)ctx->L * jb.n;
-    if (ctx->L > 12 || ctx->mont) {  // 768-bit jobs, full-width moduli: per-call kernels afterwards
+    if (!batch_tile_kind(ctx)) {  // 64, 512, 768, 1024 bits, full-width moduli: per-call kernels afterwards
       BatchDeferred d;
       d.op = jb.op;
       d.n = jb.n;
@@ -503,7 +507,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
   // shared memory: the largest transform tile of the batch
   size_t smem = 0;
   for (int j = 0; j < njobs; ++j)
-    if (jobs[j].op <= MOMA_OP_POLYMUL && jobs[j].ctx->L <= 12 && !jobs[j].ctx->mont)
+    if (jobs[j].op <= MOMA_OP_POLYMUL && batch_tile_kind(jobs[j].ctx))
       smem = std::max(smem, (size_t)jobs[j].ctx->L * 4u << kBatchTileLog);
   b->smem = smem;
   if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(12 * 4 << kBatchTileLog)) !=

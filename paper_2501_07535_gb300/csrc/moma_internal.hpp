@@ -14,7 +14,7 @@
 
 namespace moma {
 
-constexpr int kMaxL = 24;
+constexpr int kMaxL = 32;
 constexpr int kMaxLogN = 24;
 
 // Host copy of the per-modulus constants (device code receives ModK<L> by value).
@@ -83,6 +83,9 @@ moma_status launch_vec(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const
                        uint32_t* c, const uint32_t* alpha_host, cudaStream_t st);
 moma_status launch_vec_cfg(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
                            uint32_t* c, const uint32_t* alpha_host, const moma_config& cfg, cudaStream_t st);
+// moma_blas_wide.cu: 512-, 768- and 1024-bit contexts
+moma_status launch_vec_wide(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
+                            uint32_t* c, const uint32_t* alpha_host, const moma_config& cfg, cudaStream_t st);
 
 // moma_ntt.cu
 int default_tile_log(int L);
@@ -101,6 +104,12 @@ moma_status launch_polymul(moma_ctx* ctx, int logn, const uint32_t* a, const uin
 moma_status launch_polymul_cfg(moma_ctx* ctx, int logn, const uint32_t* a, const uint32_t* b,
                                uint32_t* c, const moma_config& cfg, cudaStream_t st, bool negacyclic = false);
 void free_plan(Plan* p);
+// moma_ntt_wide.cu: passes and twiddle tables of 512-, 768- and 1024-bit contexts
+moma_status run_pass_wide(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
+                          const uint32_t* src2, uint32_t* dst, uint32_t flags, const moma_config& cfg,
+                          cudaStream_t st);
+moma_status gen_table_wide(const moma_ctx* ctx, uint32_t* dst, uint64_t count, uint64_t D, uint64_t C, uint64_t S,
+                           int logn, const std::vector<BigU>& pw, const BigU& init);
 // Every pass of a plan with caller-provided intermediate buffers (s1, s2: count*L*n words each;
 // s1 may be null for a one-pass plan, s2 for plans of up to two passes).
 moma_status run_plan_buffers(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,

@@ -24,30 +24,52 @@ __device__ __forceinline__ uint32_t chunk_of(uint32_t x, int c) {
   else return (uint32_t)c;
 }
 
+// (A 64-bit container, L = 2, takes one 8-byte access per element instead.)
 template <int L>
 __device__ __forceinline__ void tile_load(const uint32_t* sm, uint32_t x, uint32_t (&v)[L]) {
-  const uint4* p = reinterpret_cast<const uint4*>(sm) + x * (L / 4);
+  if constexpr (L % 4 != 0) {
+    static_assert(L == 2, "limb counts are 2 or multiples of 4");
+    const uint2 t = reinterpret_cast<const uint2*>(sm)[x];
+    v[0] = t.x;
+    v[1] = t.y;
+    return;
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(sm) + x * (L / 4);
 #pragma unroll
-  for (int c = 0; c < L / 4; ++c) {
-    const uint4 t = p[chunk_of<L>(x, c)];
-    v[4 * c] = t.x;
-    v[4 * c + 1] = t.y;
-    v[4 * c + 2] = t.z;
-    v[4 * c + 3] = t.w;
+    for (int c = 0; c < L / 4; ++c) {
+      const uint4 t = p[chunk_of<L>(x, c)];
+      v[4 * c] = t.x;
+      v[4 * c + 1] = t.y;
+      v[4 * c + 2] = t.z;
+      v[4 * c + 3] = t.w;
+    }
   }
 }
 
 template <int L>
 __device__ __forceinline__ void tile_store(uint32_t* sm, uint32_t x, const uint32_t (&v)[L]) {
-  uint4* p = reinterpret_cast<uint4*>(sm) + x * (L / 4);
+  if constexpr (L % 4 != 0) {
+    reinterpret_cast<uint2*>(sm)[x] = make_uint2(v[0], v[1]);
+  } else {
+    uint4* p = reinterpret_cast<uint4*>(sm) + x * (L / 4);
 #pragma unroll
-  for (int c = 0; c < L / 4; ++c) p[chunk_of<L>(x, c)] = make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    for (int c = 0; c < L / 4; ++c)
+      p[chunk_of<L>(x, c)] = make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  }
 }
 
 // One twiddle entry (value and companion) from an entry-major table, L/2 16-byte loads.
 template <int L>
 __device__ __forceinline__ void twiddle_load(const uint32_t* table, uint64_t entry, uint32_t (&w)[L],
                                              uint32_t (&wp)[L]) {
+  if constexpr (L % 4 != 0) {  // L = 2: the whole entry is one 16-byte load
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(table + entry * 2 * L));
+    w[0] = a.x;
+    w[1] = a.y;
+    wp[0] = a.z;
+    wp[1] = a.w;
+    return;
+  }
   const uint4* p = reinterpret_cast<const uint4*>(table + entry * 2 * L);
 #pragma unroll
   for (int c = 0; c < L / 4; ++c) {

@@ -22,7 +22,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-WIDTHS = (128, 256, 384, 768)
+WIDTHS = (64, 128, 256, 384, 512, 768, 1024)
 _HERE = os.path.dirname(os.path.abspath(__file__))
 PRIMES_JSON = os.path.join(os.path.dirname(_HERE), "tests", "golden", "primes.json")
 

@@ -12,7 +12,7 @@ import sys
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))))
 from oracle import gen_prime, gen_prime_full, two_adicity  # noqa: E402
 
-WIDTHS = (128, 256, 384, 768)
+WIDTHS = (64, 128, 256, 384, 512, 768, 1024)
 SEEDS = (0, 1, 2, 3)
 
 

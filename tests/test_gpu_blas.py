@@ -12,7 +12,7 @@ import oracle
 from paper_2501_07535_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
-WIDTHS = [128, 256, 384, 768]
+WIDTHS = [64, 128, 256, 384, 512, 768, 1024]
 OPS = ["add", "sub", "mul", "axpy"]
 
 

@@ -43,7 +43,7 @@ def test_ntt_every_engine_and_split(gpu, width, engine):
         gpu.moma_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("width", [128, 256, 384, 768])
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 @pytest.mark.parametrize("engine", [1, 2])
 def test_blas_every_engine_and_width(gpu, width, engine):
     p = inputs.prime(width)

@@ -30,7 +30,7 @@ def _rand_vec(rng, n, q):
 
 def test_primes_table_is_prime_and_shaped():
     table = inputs.load_primes()
-    assert len(table) == 16
+    assert len(table) == 28
     for (w, s), p in table.items():
         assert sympy.isprime(p.q), (w, s)
         assert p.q.bit_length() == w - 4 == p.bits          # Sec. 5.2: W-4 bit modulus
@@ -40,7 +40,7 @@ def test_primes_table_is_prime_and_shaped():
 
 def test_primes_table_regenerates_from_oracle():
     table = inputs.load_primes()
-    for w in (128, 256, 384, 768):
+    for w in (64, 128, 256, 384, 512, 768, 1024):
         assert oracle.gen_prime(w, 0) == table[(w, 0)].q
 
 
@@ -56,7 +56,7 @@ def test_miller_rabin_matches_sympy():
 
 # ------------------------------------------------------------------ roots of unity
 
-@pytest.mark.parametrize("width", [128, 256, 384, 768])
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 def test_root_is_primitive_for_all_supported_sizes(width):
     q = inputs.prime(width).q
     for lg in range(1, 25):
@@ -68,7 +68,7 @@ def test_root_is_primitive_for_all_supported_sizes(width):
     assert pow(oracle.root_of_unity(q, 1 << 20), 2, q) == oracle.root_of_unity(q, 1 << 19)
 
 
-@pytest.mark.parametrize("width", [128, 256, 384, 768])
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 def test_generator_is_smallest_nonresidue(width):
     q = inputs.prime(width).q
     g = oracle.smallest_nonresidue(q)
@@ -103,7 +103,7 @@ def test_ntt_matches_sympy(q):
         assert oracle.ntt_inv(ref, q, w) == sympy.discrete.transforms.intt(ref, q)
 
 
-@pytest.mark.parametrize("width", [128, 256, 384, 768])
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 def test_fast_ntt_matches_brute_force(width):
     q = inputs.prime(width).q
     rng = random.Random(width)
@@ -270,13 +270,12 @@ def test_vector_forms_match_scalar_forms():
 
 # ------------------------------------------------------------------ Barrett (Sec. 3.1)
 
-@pytest.mark.parametrize("width", [64, 128, 256, 384, 768])
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 def test_barrett_steps_exact_and_one_correction(width):
     B = width - 4
     rng = random.Random(width)
     qs = [rng.randrange(1 << (B - 1), 1 << B) | 1 for _ in range(8)]
-    if width in (128, 256, 384, 768):
-        qs.append(inputs.prime(width).q)
+    qs.append(inputs.prime(width).q)
     for q in qs:
         mu = oracle.barrett_mu(q, B)
         assert mu < (1 << width)                # mu fits the W-bit container
@@ -309,7 +308,7 @@ def test_barrett_needs_full_bit_length():
 
 def test_full_width_primes_table():
     table = inputs.load_full_primes()
-    assert len(table) == 8
+    assert len(table) == 14
     for (w, s), p in table.items():
         assert sympy.isprime(p.q), (w, s)
         assert p.q.bit_length() == w == p.bits                 # fills the container
@@ -317,7 +316,7 @@ def test_full_width_primes_table():
         assert oracle.gen_prime_full(w, s) == p.q
 
 
-@pytest.mark.parametrize("width", [128, 256, 384, 768])
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 def test_montgomery_redc_is_multiplication_by_r_inverse(width):
     """REDC(T) = T R^-1 mod q (sympy's modular inverse), below 2q before its correction."""
     R = 1 << width
@@ -346,7 +345,7 @@ def test_mulmod_via_montgomery_is_the_product(width):
 
 
 def test_full_width_transform_roots():
-    for w in (128, 256, 384, 768):
+    for w in (64, 128, 256, 384, 512, 768, 1024):
         q = inputs.prime_full(w).q
         for lg in (1, 12, 24):
             n = 1 << lg
