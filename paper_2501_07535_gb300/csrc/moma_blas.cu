@@ -13,9 +13,10 @@ moma_config vec_config(const moma_ctx* ctx, int vec_op) {
   moma_config c = {0, 0, 0, 0, 0, 0};
   auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
   if (it != ctx->configs.end()) c = it->second;
-  // Karatsuba (engine 3) measured at or above schoolbook at every width for mulmod on GB300
-  // (1.00x at 256 bits up to 1.13x at 768 bits); carry chains for the other ops
-  if (c.engine == 0) c.engine = vec_op == VEC_MUL ? 3 : 1;
+  // Karatsuba (engine 3) measured at or above schoolbook for mulmod on GB300 from 64 to 768 bits
+  // (1.00x at 256 bits up to 1.2x at 768 bits; 0.9x at 1024 bits, where carry chains are kept);
+  // carry chains for the other ops
+  if (c.engine == 0) c.engine = (vec_op == VEC_MUL && ctx->L <= 24) ? 3 : 1;
   // measured on GB300 at 2^24 elements: multiplications prefer one element per thread from
   // 256 bits up, additions and axpy two; narrow widths take the widest vectors
   if (c.vec_width == 0) {

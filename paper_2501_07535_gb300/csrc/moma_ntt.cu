@@ -36,7 +36,9 @@ namespace moma {
 // batches (see the autotuner for other sizes): 128-thread CTAs on 2^10-element tiles with radix
 // up to 2^5 through 384 bits (the 384-bit kernel capped at 102 registers), 256-thread CTAs on
 // 2^11 tiles with radix 2^7 at 768 bits; the wide engine through 384 bits, carry chains above.
-// 64-, 512- and 1024-bit containers (the ends of the paper's width sweep) take 2^10 tiles.
+// The ends of the paper's width sweep: 2^10 tiles at 64 bits; 2^9 tiles at 512 and 1024 bits, so
+// that two of their CTAs (up to 255 registers per thread) fit an SM (1024 bits: 217 against 425 us
+// for a 2^16-point transform with 2^10 tiles; 512 bits: 8% faster).
 struct NttDefaults {
   int engine, tile_log, max_logr, threads, tight;
 };
@@ -46,9 +48,9 @@ static NttDefaults ntt_defaults(int L) {
     case 4: return {2, 10, 5, 128, 0};
     case 8: return {2, 10, 5, 128, 0};
     case 12: return {2, 10, 5, 128, 1};
-    case 16: return {1, 10, 5, 128, 0};
+    case 16: return {1, 9, 5, 128, 0};
     case 24: return {1, 11, 7, 256, 0};
-    default: return {1, 10, 5, 128, 0};
+    default: return {1, 9, 5, 128, 0};
   }
 }
 int default_tile_log(int L) { return ntt_defaults(L).tile_log; }
