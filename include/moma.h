@@ -58,7 +58,7 @@ typedef enum {
   MOMA_ERR_CUDA = 6,        /* a CUDA runtime call failed (launch, copy, event)      */
   MOMA_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out                    */
   MOMA_ERR_BUDGET = 8,      /* a job does not fit the memory budget it was given     */
-  MOMA_ERR_UNSUPPORTED = 9  /* valid request this build does not implement           */
+  MOMA_ERR_UNSUPPORTED = 9  /* valid request the library does not implement          */
 } moma_status;
 
 /* Human-readable name of a status code (static string, never NULL). */
