@@ -36,7 +36,8 @@ namespace moma {
 // batches (see the autotuner for other sizes): 128-thread CTAs on 2^10-element tiles with radix
 // up to 2^5 through 384 bits (the 384-bit kernel capped at 102 registers), 256-thread CTAs on
 // 2^11 tiles with radix 2^7 at 768 bits; the wide engine through 384 bits, carry chains above.
-// The ends of the paper's width sweep: 2^10 tiles at 64 bits; 2^9 tiles at 512 and 1024 bits, so
+// The ends of the paper's width sweep: 2^12 tiles with radix up to 2^7 at 64 bits (three passes for
+// 2^20 points: 10% faster than four); 2^9 tiles at 512 and 1024 bits, so
 // that two of their CTAs (up to 255 registers per thread) fit an SM (1024 bits: 217 against 425 us
 // for a 2^16-point transform with 2^10 tiles; 512 bits: 8% faster).
 struct NttDefaults {
@@ -44,7 +45,7 @@ struct NttDefaults {
 };
 static NttDefaults ntt_defaults(int L) {
   switch (L) {
-    case 2: return {2, 10, 5, 128, 0};
+    case 2: return {2, 12, 7, 256, 0};
     case 4: return {2, 10, 5, 128, 0};
     case 8: return {2, 10, 5, 128, 0};
     case 12: return {2, 10, 5, 128, 1};
