@@ -303,6 +303,37 @@ moma_status moma_ctx_get_config(moma_ctx *ctx, int op, size_t n, moma_config *cf
 moma_status moma_autotune(moma_ctx *ctx, int op, size_t n, size_t count, void *stream,
                           moma_config *best, double *best_us);
 
+/* ------------------------------------------------------------------ word-level blocks */
+
+/* Operations of moma_word_probe. */
+typedef enum {
+  MOMA_WORD_ADD = 0,     /* out = a + b: L words and the carry word (out plane L)               */
+  MOMA_WORD_SUB = 1,     /* out = a - b mod 2^W: L words and the borrow (out plane L)            */
+  MOMA_WORD_MUL = 2,     /* out = a * b: 2L words (engine 1 carry chains, 2 whole products,
+                            3 Karatsuba)                                                         */
+  MOMA_WORD_MUL_HI = 3,  /* out = the truncated high half floor(a*b / 2^W) or one less: L words
+                            (engine 1 or 2)                                                      */
+  MOMA_WORD_BARRETT = 4, /* out = a * b mod q by Barrett reduction (L words), plane L = 1 when the
+                            final correction fired (Barrett contexts; a, b canonical)            */
+  MOMA_WORD_FIXED = 5,   /* out = a * w - s * q with w = b's element 0 and s the quotient estimate
+                            from w's companion, before any correction: in [0, 3q) (Barrett
+                            contexts; w canonical; a any L-word value)                           */
+  MOMA_WORD_MONT = 6     /* out = a * b * R^-1 mod q, R = 2^W (full-width contexts; a, b < q)     */
+} moma_word_op;
+
+/* The word-level building blocks of the multi-word arithmetic (Sec. 3, Table 1 rules;
+ * Sec. 2.2 Eq. muls / Eq. mulk; Sec. 3.1 Eq. barrett), one element per thread, with their raw
+ * outputs, for tests that check each block against integer arithmetic and against the bounds
+ * the method relies on.  a, b: L*n words (limb-major, device); out: (2L+1)*n words
+ * (limb-major, device; planes not written by the operation are zero).  The context supplies
+ * the modulus and its constants; MOMA_WORD_BARRETT and MOMA_WORD_FIXED need a context made by
+ * moma_ctx_create, MOMA_WORD_MONT one made by moma_ctx_create_full (else
+ * MOMA_ERR_INVALID_ARG).  64 to 768 bits (1024-bit contexts give MOMA_ERR_UNSUPPORTED).
+ * n <= 2^30.  Asynchronous on `stream`, except MOMA_WORD_FIXED, which first reads w from the
+ * device. */
+moma_status moma_word_probe(moma_ctx *ctx, int op, int engine, size_t n, const uint32_t *a,
+                            const uint32_t *b, uint32_t *out, void *stream);
+
 /* ------------------------------------------------------------------ measurement */
 
 /* Integer multiply-add issue-rate microbenchmark (used for the compute roofline).

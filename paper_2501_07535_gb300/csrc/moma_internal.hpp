@@ -114,6 +114,9 @@ moma_status gen_table_wide(const moma_ctx* ctx, uint32_t* dst, uint64_t count, u
 // s1 may be null for a one-pass plan, s2 for plans of up to two passes).
 moma_status run_plan_buffers(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
                              uint32_t* out, const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st);
+// moma_words_wide.cu: the word-level block probe of 512- and 768-bit contexts
+moma_status run_words_wide(moma_ctx* ctx, int op, int engine, size_t n, const uint32_t* a, const uint32_t* b,
+                           uint32_t* out, cudaStream_t st);
 // Existing plan or null; never builds one (no allocation).
 Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr);
 // All passes of an existing single-transform plan with caller-provided scratch

@@ -61,6 +61,7 @@ _SIGS = {
     "moma_ctx_get_config": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _P]),
     "moma_autotune": (ctypes.c_int, [_P, ctypes.c_int, _SZ, _SZ, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "moma_ntt_fwd_noalloc": (ctypes.c_int, [_P, _SZ, _P, _P, _P]),
+    "moma_word_probe": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _SZ, _P, _P, _P, _P]),
     "moma_ntt_fwd_negacyclic": (ctypes.c_int, [_P, _SZ, _SZ, _P, _P, _P]),
     "moma_ntt_inv_negacyclic": (ctypes.c_int, [_P, _SZ, _SZ, _P, _P, _P]),
     "moma_polymul_negacyclic": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
@@ -245,6 +246,16 @@ def moma_polymul_negacyclic(ctx, n, a, b, c, stream=None):
     """c = a * b mod (x^n + 1, q)."""
     _check(lib().moma_polymul_negacyclic(ctx, n, _ptr(a), _ptr(b), _ptr(c), _stream_handle(stream)),
            "moma_polymul_negacyclic")
+
+
+WORD_OPS = {"add": 0, "sub": 1, "mul": 2, "mul_hi": 3, "barrett": 4, "fixed": 5, "mont": 6}
+
+
+def moma_word_probe(ctx, op, engine, n, a, b, out, stream=None):
+    """Raw outputs of one word-level block (op a name of WORD_OPS or its code); out: (2L+1) x n."""
+    code = WORD_OPS[op] if isinstance(op, str) else int(op)
+    _check(lib().moma_word_probe(ctx, code, engine, n, _ptr(a), _ptr(b), _ptr(out), _stream_handle(stream)),
+           "moma_word_probe")
 
 
 def moma_probe_imad(variant: int, blocks: int, threads: int, iters: int):
