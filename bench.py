@@ -522,7 +522,8 @@ def run_sensitivity(steps=5):
     (batches of 256, ns per butterfly = 2t/(n log2 n) as in Sec. 5.3), with the slowdown per
     doubling of the width as the paper reports it; (2) mulmod with schoolbook carry chains,
     whole mad.wide products and Karatsuba (Eq. mulk) at each width, 2^22 elements; (3) the same
-    mulmod and transform over a full-width modulus (Montgomery products, Sec. 5.2)."""
+    mulmod and transform over a full-width modulus: mulmod by the word-based Barrett reduction and
+    by two Montgomery products (Sec. 5.2), the transform with Montgomery twiddle products."""
     import torch
 
     from paper_2501_07535_gb300 import inputs, moma
@@ -564,18 +565,24 @@ def run_sensitivity(steps=5):
             eng[name] = round(vn / timed(lambda: moma.moma_vec_mulmod(ctx, vn, a, b, c)) / 1e6, 2)
         out["mulmod_engines"].append({"bits": w, "gelem_s": eng,
                                       "karatsuba_over_schoolbook": round(eng["karatsuba"] / eng["schoolbook_carry"], 3)})
-        # full-width modulus (W bits, Montgomery products) against the (W-4)-bit Barrett context
+        # full-width modulus (W bits) against the (W-4)-bit Barrett context: mulmod by the default
+        # word-based Barrett reduction with an (L+1)-word constant and by two Montgomery products
+        # (engine 4); transforms with Montgomery twiddle products
         pf = inputs.prime_full(w)
         fctx = moma.moma_ctx_create_full(pf.q, w)
         fa = moma.to_device(inputs.residues(pf.q, pf.L, vn, 1))
         fb = moma.to_device(inputs.residues(pf.q, pf.L, vn, 2))
+        full_gelem = vn / timed(lambda: moma.moma_vec_mulmod(fctx, vn, fa, fb, c)) / 1e6
+        moma.moma_ctx_set_config(fctx, "mul", vn, engine=4)
         mont_gelem = vn / timed(lambda: moma.moma_vec_mulmod(fctx, vn, fa, fb, c)) / 1e6
         fx = torch.zeros_like(x)
         fx[:, 0, :] = 3
         fms = timed(lambda: moma.moma_ntt_fwd_many(fctx, n, cnt, fx, y))
         out["full_width_montgomery"].append({
-            "bits": w, "mulmod_gelem_s": round(mont_gelem, 2),
-            "mulmod_over_barrett": round(mont_gelem / max(eng.values()), 3),
+            "bits": w, "mulmod_gelem_s": round(full_gelem, 2),
+            "mulmod_over_barrett": round(full_gelem / max(eng.values()), 3),
+            "mulmod_two_montgomery_gelem_s": round(mont_gelem, 2),
+            "word_barrett_over_montgomery": round(full_gelem / mont_gelem, 3),
             "ntt_n4096_ns_per_butterfly": round(fms * 1e6 / cnt * 2 / (n * 12), 4),
             "ntt_over_barrett_time": round(fms / ms, 3)})
         moma.moma_ctx_destroy(fctx)

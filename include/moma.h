@@ -268,11 +268,17 @@ typedef enum {
  *              truncated high half this way and their low halves by carry chains;
  *              3: (MOMA_OP_MUL only) the double-width product a*b by Karatsuba (Sec. 2.2
  *              Eq. mulk) down to 4-limb carry-chain schoolbook products.
+ *              In full-width contexts, MOMA_OP_MUL forms a*b by engine 1, 2 or 3 and reduces it
+ *              with a word-based Barrett reduction (an (L+1)-word constant floor(2^(2W)/q));
+ *              4: (MOMA_OP_MUL in full-width contexts only) two Montgomery products instead
+ *              (REDC(REDC(a b) (R^2 mod q)), Sec. 5.2).  Other ops of full-width contexts
+ *              ignore the engine.
  *              1 and 2 compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd);
  *              all engines give identical results.
  *   tile_log   transforms: log2 of the elements one CTA holds in shared memory.
  *   max_logr   transforms: largest radix (log2) of one Stockham pass.
- *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment).
+ *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment; full-width
+ *              contexts always take 1).
  *   cta_threads transforms: threads per CTA (32, 64, 128 or 256).  Each CTA owns one tile;
  *              small CTAs synchronise fewer warps between butterfly stages.
  *   tight_regs transforms: 1 = kernels compiled for fewer registers per thread (64 up to 256
@@ -318,7 +324,11 @@ typedef enum {
   MOMA_WORD_FIXED = 5,   /* out = a * w - s * q with w = b's element 0 and s the quotient estimate
                             from w's companion, before any correction: in [0, 3q) (Barrett
                             contexts; w canonical; a any L-word value)                           */
-  MOMA_WORD_MONT = 6     /* out = a * b * R^-1 mod q, R = 2^W (full-width contexts; a, b < q)     */
+  MOMA_WORD_MONT = 6,    /* out = a * b * R^-1 mod q, R = 2^W (full-width contexts; a, b < q)     */
+  MOMA_WORD_BARRETT_FULL = 7 /* planes 0..L: r = a*b - s*q before the final subtractions, L+1 words,
+                            in [0, 4q) (s the truncated quotient estimate from floor(2^(2W)/q));
+                            planes L+1..2L: a * b mod q.  Full-width contexts; a, b < q; the
+                            product a*b by `engine` (1, 2 or 3)                                  */
 } moma_word_op;
 
 /* The word-level building blocks of the multi-word arithmetic (Sec. 3, Table 1 rules;
@@ -327,7 +337,7 @@ typedef enum {
  * the method relies on.  a, b: L*n words (limb-major, device); out: (2L+1)*n words
  * (limb-major, device; planes not written by the operation are zero).  The context supplies
  * the modulus and its constants; MOMA_WORD_BARRETT and MOMA_WORD_FIXED need a context made by
- * moma_ctx_create, MOMA_WORD_MONT one made by moma_ctx_create_full (else
+ * moma_ctx_create, MOMA_WORD_MONT and MOMA_WORD_BARRETT_FULL one made by moma_ctx_create_full (else
  * MOMA_ERR_INVALID_ARG).  64 to 768 bits (1024-bit contexts give MOMA_ERR_UNSUPPORTED).
  * n <= 2^30.  Asynchronous on `stream`, except MOMA_WORD_FIXED, which first reads w from the
  * device. */

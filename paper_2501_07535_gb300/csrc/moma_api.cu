@@ -58,6 +58,15 @@ static moma_status ctx_create(const uint32_t* q, int bits, bool mont, moma_ctx**
     uint32_t inv = q[0];  // q^-1 mod 2^32 by Newton's iteration (q odd: q*q = 1 mod 8 to start)
     for (int i = 0; i < 5; ++i) inv *= 2u - q[0] * inv;
     c->k.qinv = 0u - inv;
+    // word-based Barrett for products of two vectors: mu = floor(2^(64L) / q) (L+1 words),
+    // 2^(32L) - q and 2q (L+1 words)
+    BigU mu, q2 = add(Q, Q);
+    divmod(pow2(2 * bits), Q, &mu, nullptr);
+    sub(W, Q).to_words(c->k.nq, L);
+    mu.to_words(c->k.mu, L);
+    c->k.mu_hi = mu.word((size_t)L);
+    q2.to_words(c->k.q2, L);
+    c->k.q2_hi = q2.word((size_t)L);
   } else {
     const int B = bits - 4;
     BigU nq = sub(W, Q);

@@ -47,9 +47,12 @@ struct VecT<4> {
 
 // ENG: 1 carry-chain rows, 2 whole-product (mad.wide) rows, 3 Karatsuba double-width product
 // (Eq. mulk, carry-chain base) for mulmod; axpy's fixed-scalar product has no double-width
-// product, so ENG 3 uses carry chains there.  ENG 4: full-width contexts (Montgomery products,
-// the sum's carry word formed; the axpy scalar arrives in Montgomery form).
-template <int L, int OP, int V, int ENG>
+// product, so ENG 3 uses carry chains there.
+// FULL: 0 a (W-4)-bit modulus (Barrett, Eq. barrett); 1 a full-width modulus, sums with their
+// carry word, mulmod by the ENG product and the word-based Barrett reduction with an (L+1)-word
+// constant; 2 a full-width modulus with mulmod as two Montgomery products.  In both full-width
+// forms the axpy scalar arrives in Montgomery form (one Montgomery product gives alpha * x).
+template <int L, int OP, int V, int ENG, int FULL = 0>
 __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArgs<L> p) {
   using VT = typename VecT<V>::T;
   const uint64_t units = p.n / V;
@@ -69,13 +72,14 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
     uint32_t z[V][L];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if constexpr (ENG == 4) {
+      if constexpr (FULL != 0) {
         if constexpr (OP == VEC_ADD) {
           addmod_full<L>(z[v], x[v], y[v], p.k.q);
         } else if constexpr (OP == VEC_SUB) {
           submod<L>(z[v], x[v], y[v], p.k.q);
         } else if constexpr (OP == VEC_MUL) {
-          mulmod_mont<L>(z[v], x[v], y[v], p.k);
+          if constexpr (FULL == 2) mulmod_mont<L>(z[v], x[v], y[v], p.k);
+          else mulmod_barrett_full<L, ENG>(z[v], x[v], y[v], p.k);
         } else {
           uint32_t ax[L];
           montmul<L>(ax, x[v], p.alpha, p.k);
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
   }
 }
 
-template <int L, int OP, int V, int ENG>
+template <int L, int OP, int V, int ENG, int FULL = 0>
 moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
                            const uint32_t* alpha_host, cudaStream_t st) {
   VecArgs<L> p;
@@ -119,7 +123,7 @@ moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* 
   if (OP == VEC_AXPY) {
     BigU al = BigU::from_words(alpha_host, L);
     if (cmp(al, ctx->Q) >= 0) return MOMA_ERR_INVALID_ARG;
-    if (ENG == 4) {  // alpha R mod q: one Montgomery product gives alpha * x
+    if (FULL != 0) {  // alpha R mod q: one Montgomery product gives alpha * x
       ctx->red->mulmod(al, BigU::from_words(ctx->k.R0, L)).to_words(p.alpha, L);
     } else {
       al.to_words(p.alpha, L);
@@ -129,7 +133,7 @@ moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* 
   static int occ = -1;  // per-instantiation occupancy, computed once
   if (occ < 0) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V, ENG>, 256, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V, ENG, FULL>, 256, 0) != cudaSuccess)
       return MOMA_ERR_CUDA;
     occ = o > 0 ? o : 1;
   }
@@ -138,7 +142,7 @@ moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* 
   const uint64_t cap = (uint64_t)ctx->num_sms * (uint64_t)occ;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) return MOMA_OK;
-  vec_kernel<L, OP, V, ENG><<<(unsigned)blocks, 256, 0, st>>>(p);
+  vec_kernel<L, OP, V, ENG, FULL><<<(unsigned)blocks, 256, 0, st>>>(p);
   return cuda_status(cudaGetLastError());
 }
 
@@ -159,12 +163,16 @@ moma_status dispatch_op(moma_ctx* ctx, int op, size_t n, const uint32_t* a, cons
                                const uint32_t* alpha, const moma_config& cfg, cudaStream_t st) {
   const int eng = cfg.engine;
   const int vw = cfg.vec_width;
-  if (ctx->mont) {  // full-width modulus: Montgomery, one element per thread
+  if (ctx->mont) {  // full-width modulus, one element per thread
     switch (op) {
-      case VEC_ADD: return run_vec<L, VEC_ADD, 1, 4>(ctx, n, a, b, c, alpha, st);
-      case VEC_SUB: return run_vec<L, VEC_SUB, 1, 4>(ctx, n, a, b, c, alpha, st);
-      case VEC_MUL: return run_vec<L, VEC_MUL, 1, 4>(ctx, n, a, b, c, alpha, st);
-      case VEC_AXPY: return run_vec<L, VEC_AXPY, 1, 4>(ctx, n, a, b, c, alpha, st);
+      case VEC_ADD: return run_vec<L, VEC_ADD, 1, 1, 1>(ctx, n, a, b, c, alpha, st);
+      case VEC_SUB: return run_vec<L, VEC_SUB, 1, 1, 1>(ctx, n, a, b, c, alpha, st);
+      case VEC_MUL:
+        return eng == 4   ? run_vec<L, VEC_MUL, 1, 1, 2>(ctx, n, a, b, c, alpha, st)
+               : eng == 3 ? run_vec<L, VEC_MUL, 1, 3, 1>(ctx, n, a, b, c, alpha, st)
+               : eng == 2 ? run_vec<L, VEC_MUL, 1, 2, 1>(ctx, n, a, b, c, alpha, st)
+                          : run_vec<L, VEC_MUL, 1, 1, 1>(ctx, n, a, b, c, alpha, st);
+      case VEC_AXPY: return run_vec<L, VEC_AXPY, 1, 1, 2>(ctx, n, a, b, c, alpha, st);
     }
     return MOMA_ERR_INVALID_ARG;
   }

@@ -18,6 +18,8 @@ inline void fill_modk(const moma_ctx* ctx, ModK<L>& k) {
     k.r2[i] = ctx->k.r2[i];
   }
   k.qinv = ctx->k.qinv;
+  k.mu_hi = ctx->k.mu_hi;
+  k.q2_hi = ctx->k.q2_hi;
 }
 
 }  // namespace moma

@@ -25,6 +25,8 @@ struct HostConsts {
   uint32_t Q0 = 0;          // floor(2^(32L) / q)  (between 16 and 31 for a W-4 bit q)
   uint32_t r2[kMaxL] = {};  // full-width contexts: 2^(64L) mod q
   uint32_t qinv = 0;        // full-width contexts: -q^-1 mod 2^32
+  uint32_t mu_hi = 0;       // full-width contexts: word L of floor(2^(64L) / q)
+  uint32_t q2_hi = 0;       // full-width contexts: word L of 2q
 };
 
 // One Stockham pass: radix 2^logR over groups of stride n/R, after logNs radix bits.

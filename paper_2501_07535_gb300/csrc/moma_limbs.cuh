@@ -397,11 +397,14 @@ template <int L>
 struct ModK {
   uint32_t q[L];    // modulus, B = 32L - 4 bits (full-width contexts: up to 32L bits)
   uint32_t nq[L];   // 2^(32L) - q, so that  t - s*q = t + s*nq  mod 2^(32L)
-  uint32_t mu[L];   // Barrett constant floor(2^(2B+3) / q)  (Eq. mu, k = 2B+3)
-  uint32_t q2[L];   // 2q
+  uint32_t mu[L];   // Barrett constant floor(2^(2B+3) / q)  (Eq. mu, k = 2B+3); full-width
+                    // contexts: the low L words of floor(2^(64L) / q)
+  uint32_t q2[L];   // 2q (full-width contexts: its low L words)
   uint32_t q4[L];   // 4q: bound of the lazy (not fully reduced) values inside a transform
   uint32_t r2[L];   // full-width contexts: R^2 mod q, R = 2^(32L)
   uint32_t qinv;    // full-width contexts: -q^-1 mod 2^32
+  uint32_t mu_hi;   // full-width contexts: word L of floor(2^(64L) / q)  (>= 1)
+  uint32_t q2_hi;   // full-width contexts: word L of 2q  (0 or 1)
 };
 
 // ------------------------------------------------------------------ Sec. 3.1, Eq. barrett
@@ -494,7 +497,10 @@ MOMA_DEV void mulmod_fixed(uint32_t (&r)[L], const uint32_t (&a)[L], const uint3
 // ------------------------------------------------------------------ full-width moduli
 // A modulus that fills its container (up to B = W bits) leaves no headroom: a + b can carry out
 // of the W bits, and the Barrett constants above no longer fit.  Sec. 5.2 names Montgomery
-// reduction for this case.  Values stay canonical; R = 2^W.
+// reduction for this case: twiddles and scalars use it (one Montgomery product by a constant kept
+// in Montgomery form).  The product of two canonical vectors takes a word-based Barrett reduction
+// with an (L+1)-word constant instead (barrett_reduce_full), which needs about half the word
+// products of the two Montgomery products it replaces.  Values stay canonical; R = 2^W.
 
 // c = a + b mod q for canonical a, b < q < 2^W: the carry word of rule (moddq_add) is formed
 // (the sum may need W+1 bits); subtract q when the sum carried out or is >= q.
@@ -549,6 +555,68 @@ MOMA_DEV void mulmod_mont(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32
   uint32_t t[L];
   montmul<L>(t, a, b, k);
   montmul<L>(c, t, k.r2, k);
+}
+
+// Word-based Barrett reduction for a modulus that fills its container.  Base b = 2^32; q has L
+// words with a nonzero top word, so b^(L-1) < q < b^L (q odd); mu = floor(b^(2L) / q) then has
+// L+1 words, b^L < mu < b^(L+1).  For t < q^2:
+//   q1 = floor(t / b^(L-1))        words L-1 .. 2L-1 of t (no shift);
+//   s ~= floor(q1 mu / b^(L+1))    the truncated high half of q1 mu (exact floor or one less);
+//   r = t - s q                    formed mod b^(L+1) as t + s (b^(L+1) - q).
+// With Q = floor(t / q): q1 > t/b^(L-1) - 1 and mu > b^(2L)/q - 1 give q1 mu / b^(L+1) in
+// (t/q - t/b^(2L) - b^(L-1)/q, t/q], an interval of length below 2, so its floor is Q, Q-1 or Q-2;
+// the truncation takes at most one more, hence s in [Q-3, Q] (s < q < b^L: one word fewer than
+// q1 mu's high half) and r in [0, 4q), exact in L+1 words.  Two conditional subtractions (2q,
+// then q) end it.  Besides the product t: about (L+1)^2 / 2 word products for s and as many for
+// the low half of s q, against 2L^2 + L for one Montgomery product (a canonical product needs two).
+// r_raw returns r before the subtractions.
+template <int L>
+MOMA_DEV void barrett_reduce_full(uint32_t (&c)[L], uint32_t (&r_raw)[L + 1], const uint32_t (&t)[2 * L],
+                                  const ModK<L>& k) {
+  uint32_t q1[L + 1], mu[L + 1], h[L + 1];
+#pragma unroll
+  for (int i = 0; i <= L; ++i) q1[i] = t[L - 1 + i];
+#pragma unroll
+  for (int i = 0; i < L; ++i) mu[i] = k.mu[i];
+  mu[L] = k.mu_hi;
+  mul_hi_trunc<L + 1>(h, q1, mu);  // words L+1 .. 2L+1 of q1 mu; h[L] = 0 since s < b^L
+  uint32_t s[L + 1], nq1[L + 1], r[L + 1];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    s[i] = h[i];
+    nq1[i] = k.nq[i];
+  }
+  s[L] = 0u;
+  nq1[L] = 0xffffffffu;  // b^(L+1) - q = (b - 1) b^L + (b^L - q)
+#pragma unroll
+  for (int i = 0; i <= L; ++i) r[i] = t[i];
+  mul_lo_acc<L + 1>(r, s, nq1);
+#pragma unroll
+  for (int i = 0; i <= L; ++i) r_raw[i] = r[i];
+  uint32_t m[L + 1];
+#pragma unroll
+  for (int i = 0; i < L; ++i) m[i] = k.q2[i];
+  m[L] = k.q2_hi;
+  cond_sub<L + 1>(r, m);  // [0, 4q) -> [0, 2q)
+#pragma unroll
+  for (int i = 0; i < L; ++i) m[i] = k.q[i];
+  m[L] = 0u;
+  cond_sub<L + 1>(r, m);  // -> [0, q)
+#pragma unroll
+  for (int i = 0; i < L; ++i) c[i] = r[i];
+}
+
+// c = a b mod q for canonical a, b under a full-width modulus: the double-width product by
+// engine ENG (1 carry chains, 2 whole products, 3 Karatsuba), then barrett_reduce_full.
+template <int L, int ENG>
+MOMA_DEV void mulmod_barrett_full(uint32_t (&c)[L], const uint32_t (&a)[L], const uint32_t (&b)[L],
+                                  const ModK<L>& k) {
+  uint32_t t[2 * L];
+  if constexpr (ENG == 3) mul_full_k<L>(t, a, b);
+  else if constexpr (ENG == 2) mul_full_w<L>(t, a, b);
+  else mul_full<L>(t, a, b);
+  uint32_t r[L + 1];
+  barrett_reduce_full<L>(c, r, t, k);
 }
 
 }  // namespace moma

@@ -32,7 +32,8 @@ extern "C" moma_status moma_ctx_set_config(moma_ctx* ctx, int op, size_t n, cons
     return MOMA_OK;
   }
   if (is_vec_op(op)) {
-    if (cfg->engine < 0 || cfg->engine > 3) return MOMA_ERR_INVALID_ARG;
+    if (cfg->engine < 0 || cfg->engine > 4) return MOMA_ERR_INVALID_ARG;
+    if (cfg->engine == 4 && !(ctx->mont && op == MOMA_OP_MUL)) return MOMA_ERR_INVALID_ARG;
     if (cfg->vec_width != 0 && cfg->vec_width != 1 && cfg->vec_width != 2 && cfg->vec_width != 4)
       return MOMA_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->lock);
@@ -109,9 +110,11 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
         }
   } else if (is_vec_op(op)) {
     if (n == 0) return MOMA_ERR_SIZE;
-    const int engines = op == MOMA_OP_MUL ? 3 : (op == MOMA_OP_AXPY ? 2 : 1);
+    // full-width contexts: one element per thread, and mulmod's engine 4 (two Montgomery products)
+    const int engines = op == MOMA_OP_MUL ? (ctx->mont ? 4 : 3) : (op == MOMA_OP_AXPY && !ctx->mont ? 2 : 1);
+    const int vmax = ctx->mont ? 1 : vec_max_width(ctx->L);
     for (int engine = 1; engine <= engines; ++engine)
-      for (int v = 1; v <= vec_max_width(ctx->L); v *= 2) cands.push_back({engine, 0, 0, v, 0, 0});
+      for (int v = 1; v <= vmax; v *= 2) cands.push_back({engine, 0, 0, v, 0, 0});
   } else {
     return MOMA_ERR_INVALID_ARG;
   }

@@ -9,7 +9,9 @@
 //   - Barrett reduction of a*b with the flag of its final correction (Sec. 3.1 Eq. barrett: one
 //     correction suffices for a (W-4)-bit modulus);
 //   - the fixed-multiplicand product before its corrections (a value in [0, 3q));
-//   - the Montgomery product a b R^-1 mod q (full-width contexts).
+//   - the Montgomery product a b R^-1 mod q (full-width contexts);
+//   - the word-based Barrett reduction of full-width contexts: r before its two subtractions
+//     (L+1 words, below 4q) and the reduced product.
 // moma_words.cu instantiates them up to 384 bits, moma_words_wide.cu from 512 bits.
 #pragma once
 #include "moma_consts.cuh"
@@ -90,6 +92,18 @@ __global__ void __launch_bounds__(256) word_kernel(const __grid_constant__ WordA
       else mulmod_fixed_lazy<L, false>(r, a, p.w, p.wp, p.k);
 #pragma unroll
       for (int l = 0; l < L; ++l) o[l] = r[l];
+      break;
+    }
+    case MOMA_WORD_BARRETT_FULL: {
+      uint32_t t[2 * L], c[L], r[L + 1];
+      if (p.engine == 3) mul_full_k<L>(t, a, b);
+      else if (p.engine == 2) mul_full_w<L>(t, a, b);
+      else mul_full<L>(t, a, b);
+      barrett_reduce_full<L>(c, r, t, p.k);
+#pragma unroll
+      for (int l = 0; l <= L; ++l) o[l] = r[l];
+#pragma unroll
+      for (int l = 0; l < L; ++l) o[L + 1 + l] = c[l];
       break;
     }
     default: {  // MOMA_WORD_MONT

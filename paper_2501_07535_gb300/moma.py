@@ -248,7 +248,7 @@ def moma_polymul_negacyclic(ctx, n, a, b, c, stream=None):
            "moma_polymul_negacyclic")
 
 
-WORD_OPS = {"add": 0, "sub": 1, "mul": 2, "mul_hi": 3, "barrett": 4, "fixed": 5, "mont": 6}
+WORD_OPS = {"add": 0, "sub": 1, "mul": 2, "mul_hi": 3, "barrett": 4, "fixed": 5, "mont": 6, "barrett_full": 7}
 
 
 def moma_word_probe(ctx, op, engine, n, a, b, out, stream=None):

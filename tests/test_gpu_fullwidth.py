@@ -230,3 +230,44 @@ def test_full_width_autotune(gpu, fctx):
     gpu.moma_ntt_fwd(h, n, dx, dy)
     torch.cuda.synchronize()
     assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), q)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_full_width_mulmod_engines_and_moduli(gpu, width):
+    """mulmod of full-width contexts by each product engine with the word-based Barrett reduction
+    and by two Montgomery products (engine 4): identical, and equal to a * b mod q, for the test
+    prime, an odd modulus whose top word is 1 and 2^W - 1."""
+    import random
+    rng = random.Random(width * 11)
+    L = width // 32
+    n = 3001
+    for q in (inputs.prime_full(width).q, (1 << (width - 32)) + 12345, (1 << width) - 1):
+        h = gpu.moma_ctx_create_full(q, width)
+        try:
+            a = _edge_values(q, width, rng, n)
+            b = _edge_values(q, width, rng, n)
+            want = [x * y % q for x, y in zip(a, b)]
+            da, db = gpu.to_device(inputs.from_ints(a, L)), gpu.to_device(inputs.from_ints(b, L))
+            for engine in (1, 2, 3, 4):
+                gpu.moma_ctx_set_config(h, "mul", n, engine=engine)
+                assert gpu.moma_ctx_get_config(h, "mul", n)["engine"] == engine
+                dc = torch.empty_like(da)
+                gpu.moma_vec_mulmod(h, n, da, db, dc)
+                torch.cuda.synchronize()
+                assert inputs.to_ints(gpu.to_host(dc)) == want, (hex(q), engine)
+        finally:
+            gpu.moma_ctx_destroy(h)
+
+
+def test_montgomery_engine_only_for_full_width_mulmod(gpu, fctx):
+    q = inputs.prime(256).q
+    h = gpu.moma_ctx_create(q, 256)
+    try:
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(h, "mul", 1024, engine=4)
+    finally:
+        gpu.moma_ctx_destroy(h)
+    with pytest.raises(gpu.MomaError):
+        gpu.moma_ctx_set_config(fctx[256], "add", 1024, engine=4)
+    with pytest.raises(gpu.MomaError):
+        gpu.moma_ctx_set_config(fctx[256], "mul", 1024, engine=5)

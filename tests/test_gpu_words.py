@@ -8,7 +8,10 @@ relies on (through moma_word_probe, raw outputs before any final reduction).
 - Barrett reduction (Sec. 3.1 Eq. barrett): the exact residue, and its final correction fires at
   most once (one conditional subtraction suffices for a (W-4)-bit modulus);
 - the fixed-multiplicand product before its corrections: congruent to a*w and below 3q;
-- the Montgomery product: a*b*R^-1 mod q (full-width contexts).
+- the Montgomery product: a*b*R^-1 mod q (full-width contexts);
+- the word-based Barrett reduction of full-width contexts: r = a*b - s*q before its two final
+  subtractions lies in [0, 4q) with s within 3 of floor(a*b/q), and the reduced product is exact,
+  for moduli whose top word is 1 (the largest constant floor(2^(2W)/q)) and for 2^W - 1.
 Operands are edge values (0, 1, all-ones words, q - 1, 2^W - 1 where allowed) and seeded draws.
 """
 import random
@@ -121,3 +124,32 @@ def test_word_montgomery(gpu, width):
             _probe(gpu, ctx, "barrett", 1, a[:4], b[:4], L)
     finally:
         gpu.moma_ctx_destroy(ctx)
+
+
+def _full_moduli(width):
+    """Odd full-width moduli (BLAS needs no prime): the test prime, the smallest top word, 2^W - 1."""
+    return [inputs.prime_full(width).q, (1 << (width - 32)) + 12345, (1 << width) - 1]
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_word_barrett_full_bound(gpu, width):
+    L = width // 32
+    rng = random.Random(width + 3)
+    for q in _full_moduli(width):
+        ctx = gpu.moma_ctx_create_full(q, width)
+        try:
+            n = 1500
+            a, b = _vals(width, q, rng, n), _vals(width, q, rng, n)
+            want = [x * y % q for x, y in zip(a, b)]
+            for engine in (1, 2, 3):
+                o = _probe(gpu, ctx, "barrett_full", engine, a, b, L)
+                r = _planes(o, 0, L + 1)
+                assert _planes(o, L + 1, 2 * L + 1) == want, (hex(q), engine)
+                for x, y, v in zip(a, b, r):
+                    t = x * y
+                    assert 0 <= v < 4 * q and (t - v) % q == 0, (hex(q), engine)
+                    assert t // q - 3 <= (t - v) // q <= t // q
+            with pytest.raises(gpu.MomaError):  # the W-4 bit Barrett block needs a Barrett context
+                _probe(gpu, ctx, "barrett", 1, a[:4], b[:4], L)
+        finally:
+            gpu.moma_ctx_destroy(ctx)
