@@ -407,7 +407,8 @@ def run_profile(args):
     """Small cases for ncu captures (each op: one untimed call first, then `steps` calls):
     ntt: batched forward 256-bit 2^20 NTTs; mul / add / axpy: the 2^24-element 256-bit vector op;
     ntt768: 768-bit 2^16 NTTs (batch 8); mont_ntt / mont_mul: the 256-bit NTT and mulmod over a
-    full-width modulus; batch: the uneven batch at reduced sizes (2^10..2^16, 64 jobs); batch_large:
+    full-width modulus (its context's default schedule: Montgomery twiddles, word-based Barrett
+    mulmod); mont_mul_redc: the same mulmod as two Montgomery products (engine 4); batch: the uneven batch at reduced sizes (2^10..2^16, 64 jobs); batch_large:
     128 jobs of the uneven mix at its full size range (2^10..2^20)."""
     import numpy as np
     import torch
@@ -430,11 +431,14 @@ def run_profile(args):
         print(json.dumps({"profile": op, "jobs": nj, "calls": 1 + args.steps, "status": status}))
         return
     full = op.startswith("mont_")
+    redc = op == "mont_mul_redc"
     width = 768 if op == "ntt768" else WIDTH
     p = inputs.prime_full(width) if full else inputs.prime(width)
     q, Lw = p.q, p.L
     ctx = (moma.moma_ctx_create_full if full else moma.moma_ctx_create)(q, width)
-    if op in ("mul", "add", "axpy", "mont_mul"):
+    if op in ("mul", "add", "axpy", "mont_mul", "mont_mul_redc"):
+        if redc:
+            moma.moma_ctx_set_config(ctx, "mul", VEC_N, engine=4)
         a = moma.to_device(inputs.residues(q, Lw, VEC_N, seed=1))
         b = moma.to_device(inputs.residues(q, Lw, VEC_N, seed=2))
         c = torch.empty_like(a)
@@ -684,7 +688,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small NTT-only case for ncu captures")
     ap.add_argument("--ntt-batch", type=int, default=8)
     ap.add_argument("--profile-op", default="ntt",
-                    choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "batch", "batch_large"])
+                    choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "mont_mul_redc", "batch",
+                             "batch_large"])
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
