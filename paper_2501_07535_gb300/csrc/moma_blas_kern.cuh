@@ -130,12 +130,14 @@ moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* 
       companion(ctx, al, p.alphap);
     }
   }
-  static int occ = -1;  // per-instantiation occupancy, computed once
+  static std::atomic<int> occ_cached{-1};  // per-instantiation occupancy, computed once
+  int occ = occ_cached.load(std::memory_order_relaxed);
   if (occ < 0) {
     int o = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, vec_kernel<L, OP, V, ENG, FULL>, 256, 0) != cudaSuccess)
       return MOMA_ERR_CUDA;
     occ = o > 0 ? o : 1;
+    occ_cached.store(occ, std::memory_order_relaxed);
   }
   const uint64_t units = n / V;
   uint64_t blocks = (units + 255) / 256;

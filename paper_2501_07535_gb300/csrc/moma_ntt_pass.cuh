@@ -127,12 +127,13 @@ moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t co
   NttPassArgs<L> a;
   fill_pass_args<L>(ctx, pl, d, count, src, src2, dst, flags, a);
   const size_t smem = (size_t)L * 4u << (d.logR + d.logG);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::atomic<uint64_t> attr_done{0};  // one bit per device: the attribute is per device
+  const uint64_t dev_bit = 1ull << (ctx->device & 63);
+  if (!(attr_done.load(std::memory_order_acquire) & dev_bit)) {
     if (cudaFuncSetAttribute(ntt_pass_kernel<L, WIDE, TIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              L * 4 << max_tile_log(L)) != cudaSuccess)
       return MOMA_ERR_CUDA;
-    attr_done = true;
+    attr_done.fetch_or(dev_bit, std::memory_order_release);
   }
   const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
   if (grid == 0) return MOMA_OK;
@@ -147,12 +148,13 @@ moma_status run_pass_mont(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size
   NttPassArgs<L> a;
   fill_pass_args<L>(ctx, pl, d, count, src, src2, dst, flags, a);
   const size_t smem = (size_t)L * 4u << (d.logR + d.logG);
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::atomic<uint64_t> attr_done{0};  // one bit per device: the attribute is per device
+  const uint64_t dev_bit = 1ull << (ctx->device & 63);
+  if (!(attr_done.load(std::memory_order_acquire) & dev_bit)) {
     if (cudaFuncSetAttribute(ntt_pass_mont_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              L * 4 << max_tile_log(L)) != cudaSuccess)
       return MOMA_ERR_CUDA;
-    attr_done = true;
+    attr_done.fetch_or(dev_bit, std::memory_order_release);
   }
   const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
   if (grid == 0) return MOMA_OK;
