@@ -604,8 +604,9 @@ def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
     size-class micro-batches (serve.Scheduler policy "class").  Capacity is measured closed-loop
     (all requests present at t = 0); the open-loop runs offer load x capacity, twice under each
     policy (size classes, plain FIFO micro-batches), alternating; the lower-p99 run of each is
-    reported with both runs' p99 beside it.  The same jobs as plain per-call launches give the
-    per-call throughput."""
+    reported with both runs' p99 beside it; one more run each at 0.5 and 1.0 x capacity gives the
+    latency against the offered load.  The same jobs as plain per-call launches give the per-call
+    throughput."""
     import torch
 
     from paper_2501_07535_gb300 import batch, serve
@@ -628,13 +629,22 @@ def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
         opened, fifo = (sorted(runs[pol], key=lambda r: r["p99_ms"])[0] for pol in ("class", "fifo"))
         opened["p99_ms_runs"] = [r["p99_ms"] for r in runs["class"]]
         fifo["p99_ms_runs"] = [r["p99_ms"] for r in runs["fifo"]]
+        # the same arrivals at half and at full capacity (size classes, one run each)
+        sweep = []
+        for lo in (0.5, 1.0):
+            r = serve.serve([a / (lo * capacity) for a in unit_arrivals], jobs, ctxs, slots=slots, executor=ex,
+                            policy="class").summary()
+            sweep.append({"offered_load": lo, "offered_jobs_per_s": round(lo * capacity, 1),
+                          "jobs_per_s": r["jobs_per_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                          "mean_ms": r["mean_ms"]})
+        torch.cuda.synchronize()
         plain_s = serve.run_plain(jobs, ex)
         return {"jobs": n_jobs, "policy": "class", "capacity_jobs_per_s": capacity,
                 "plain_per_call_jobs_per_s": round(n_jobs / plain_s, 1),
                 "served_over_plain": round(capacity / (n_jobs / plain_s), 3), "offered_load": load,
                 "offered_jobs_per_s": round(rate, 1), "closed_loop": closed, "open_loop": opened,
-                "open_loop_fifo": fifo, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"], "budget_gb": 40,
-                "slots": slots}
+                "open_loop_fifo": fifo, "load_sweep": sweep, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"],
+                "budget_gb": 40, "slots": slots}
     finally:
         ctxs.close()
 
