@@ -53,6 +53,37 @@ def word_products_per_mulmod(L):
     return 2 * L * L + L
 
 
+def product_peak(sms, sm_mhz):
+    """Unit-count integer-multiply peak in word products per second."""
+    return sms * PRODUCTS_PER_CLK_PER_SM * sm_mhz * 1e6
+
+
+def ntt_roofline(n, limbs, batch, step_s, prod_peak):
+    """Transform region: algorithmic word products per second ((n/2) log2 n mulmods of 2L^2 + L
+    products for each of `batch` transforms in `step_s` seconds) against the product peak."""
+    logn = n.bit_length() - 1
+    prod = word_products_per_mulmod(limbs) * (n // 2) * logn * batch
+    achieved = prod / step_s / 1e12
+    peak = prod_peak / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "T word-products/s",
+            "frac": round(achieved / peak, 4)}
+
+
+def vec_roofline(limbs, n, step_s, hbm_gbs, prod_peak, products=True):
+    """Element-wise op over n elements in `step_s` seconds: the roofline time is the slower of its
+    bytes (two operands read, one written) at the HBM peak and, for products, its 2L^2 + L word
+    products per element at the product peak."""
+    nbytes = 3 * 4 * limbs * n
+    prod = word_products_per_mulmod(limbs) * n if products else 0
+    t_hbm = nbytes / (hbm_gbs * 1e9) if hbm_gbs else 0.0
+    t_prod = prod / prod_peak
+    roof = max(t_hbm, t_prod)
+    return {"bound": "hbm" if t_hbm >= t_prod else "alu", "time_us": round(roof * 1e6, 2),
+            "achieved_us": round(step_s * 1e6, 2), "frac": round(roof / step_s, 4),
+            "hbm_gbs_achieved": round(nbytes / step_s / 1e9, 1), "hbm_gbs_peak": hbm_gbs,
+            "products_t_achieved": round(prod / step_s / 1e12, 3), "products_t_peak": round(prod_peak / 1e12, 3)}
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def _oracle_ntt_worker(args):
@@ -222,7 +253,7 @@ def run_ours(args):
         probe[variant] = pops * per_op / (pms * 1e-3)
     probe_peak = max(probe.values())  # word products / s, fastest form measured in this run
     sm_max_mhz = _measured_peaks().get("sm_max_mhz") or 2070.0
-    prod_peak = sms * PRODUCTS_PER_CLK_PER_SM * sm_max_mhz * 1e6  # unit-count peak at the max SM clock
+    prod_peak = product_peak(sms, sm_max_mhz)  # unit-count peak at the max SM clock
 
     # ---- NTT region
     def ntt_step():
@@ -268,15 +299,8 @@ def run_ours(args):
 
     # ---- roofline
     hbm = _measured_peaks().get("hbm_gbs")
-    mulmods_per_ntt = (n // 2) * LOGN
-    ntt_prod = word_products_per_mulmod(L) * mulmods_per_ntt * NTT_BATCH
-    ntt_s_per_step = ntt_ms * 1e-3 / args.steps
-    ntt_achieved = ntt_prod / ntt_s_per_step / 1e12
-    peak_t = prod_peak / 1e12
-    mul_bytes = 3 * 4 * L * VEC_N
-    mul_prod = word_products_per_mulmod(L) * VEC_N
-    mul_s = mul_ms * 1e-3 / args.steps
-    mul_roof_s = max(mul_bytes / (hbm * 1e9) if hbm else 0.0, mul_prod / prod_peak)
+    roof = ntt_roofline(n, L, NTT_BATCH, ntt_ms * 1e-3 / args.steps, prod_peak)
+    mul_roof = vec_roofline(L, VEC_N, mul_ms * 1e-3 / args.steps, hbm, prod_peak)
     launches = args.steps * n_pass_launches  # pass kernels in the timed NTT region
     c4 = run_uneven_batch(max(3, args.steps // 2), 2)
     c5 = run_served(n_jobs=args.serve_jobs) if args.serve_jobs > 0 else None
@@ -300,25 +324,18 @@ def run_ours(args):
                    "n": n, "bits": WIDTH, "limbs": L, "batch": NTT_BATCH, "vec_n": VEC_N,
                    "l2": "inputs larger than L2 (512 MiB per NTT step, 1.5 GiB per mulmod step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "achieved": round(ntt_achieved, 3), "peak": round(peak_t, 3),
-                     "unit": "T word-products/s", "frac": round(ntt_achieved / peak_t, 4),
+        "roofline": {**roof,
                      "traffic": NTT_PASS_TRAFFIC_BYTES if all(ntt_cfg.get(k) == v for k, v in
                                                               NTT_PASS_TRAFFIC_SCHEDULE.items()) else None,
                      "peak_source": f"{sms} SMs x {PRODUCTS_PER_CLK_PER_SM} whole 32x32->64 products (mad.wide) "
                                     f"per clock per SM x {sm_max_mhz:.0f} MHz max SM clock",
                      "peak_probe": round(probe_peak / 1e12, 3),
-                     "frac_of_probe": round(ntt_achieved / (probe_peak / 1e12), 4),
+                     "frac_of_probe": round(roof["achieved"] / (probe_peak / 1e12), 4),
                      "algorithmic": f"(n/2)log2(n) mulmods x (2L^2+L) = {word_products_per_mulmod(L)} word "
                                     f"products per mulmod, {NTT_BATCH} transforms per step"},
         "mulmod": {"value": round(gelem, 3), "unit": "Gelem/s", "ms_per_step": round(mul_ms / args.steps, 4),
                    "gpu_launches": args.steps,
-                   "roofline": {"bound": "hbm" if mul_bytes / (hbm * 1e9 if hbm else 1) >= mul_prod / prod_peak
-                                else "alu",
-                                "time_us": round(mul_roof_s * 1e6, 2), "achieved_us": round(mul_s * 1e6, 2),
-                                "frac": round(mul_roof_s / mul_s, 4),
-                                "hbm_gbs_achieved": round(mul_bytes / mul_s / 1e9, 1), "hbm_gbs_peak": hbm,
-                                "products_t_achieved": round(mul_prod / mul_s / 1e12, 3),
-                                "products_t_peak": round(peak_t, 3)}},
+                   "roofline": mul_roof},
         "batched_vs_plain": c4,
         "served": c5,
         "sensitivity": sens,
