@@ -39,7 +39,7 @@ L = WIDTH // 32
 # DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20)
 # from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule
 # and kernel version (None otherwise).
-NTT_PASS_TRAFFIC_BYTES = 970_086_400
+NTT_PASS_TRAFFIC_BYTES = 962_203_648
 NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 2, "tile_log": 10, "max_logr": 5, "cta_threads": 128, "tight_regs": 0}
 
 # Integer-multiply peak from the unit counts: the multiply pipe (fmaheavy) of each of the 4 SM
