@@ -12,7 +12,7 @@ not the word-level algorithm that the GPU runs.
 Citations are to the paper "Code Generation for Cryptographic Kernels using
 Multi-word Modular Arithmetic on GPU" (Zhang & Franchetti, CGO'25).
 
-Readings where the paper is silent or inconsistent (each listed in the design doc):
+Readings where the paper is silent or inconsistent:
   * addmod subtracts q when a + b >= q (Eq. saddmod prints '>', which would return q
     for a + b == q and leave Z_q); results are always canonical in [0, q).
   * The Barrett shift amount k of Eq. mu is taken as 2*MBITS + 3, matching the
