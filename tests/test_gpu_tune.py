@@ -43,6 +43,40 @@ def test_ntt_every_engine_and_split(gpu, width, engine):
         gpu.moma_ctx_destroy(ctx)
 
 
+WIDE_SCHEDULES = {
+    # (log2 n, tile_log, max_logr, cta_threads, tight_regs); tiles within shared memory at each width
+    512: ((13, 10, 5, 128, 0), (14, 11, 6, 256, 0), (12, 9, 4, 64, 0)),
+    768: ((13, 9, 4, 128, 1), (14, 10, 5, 128, 1), (13, 11, 7, 256, 0), (12, 10, 5, 64, 0), (11, 8, 4, 32, 1)),
+    1024: ((13, 9, 5, 128, 0), (12, 10, 6, 256, 0)),
+}
+
+
+@pytest.mark.parametrize("width", [512, 768, 1024])
+@pytest.mark.parametrize("engine", [1, 2])
+def test_ntt_wide_schedules(gpu, width, engine):
+    """Schedules other than the default at 512 to 1024 bits (the autotuner's candidates), forward
+    against the oracle and round trip; from 512 bits the whole-product rows and the register cap
+    exist at 768 bits only, elsewhere they fall back to carry chains."""
+    p = inputs.prime(width)
+    ctx = gpu.moma_ctx_create(p.q, width)
+    try:
+        for lg, tile, rmax, th, tight in WIDE_SCHEDULES[width]:
+            n = 1 << lg
+            kw = dict(engine=engine, tile_log=tile, max_logr=rmax, cta_threads=th, tight_regs=tight)
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", n, **kw)
+            gpu.moma_ctx_set_config(ctx, "ntt_inv", n, **kw)
+            x = inputs.residues(p.q, p.L, n, seed=lg + 7 * engine)
+            dx = gpu.to_device(x)
+            dy, dz = torch.empty_like(dx), torch.empty_like(dx)
+            gpu.moma_ntt_fwd(ctx, n, dx, dy)
+            gpu.moma_ntt_inv(ctx, n, dy, dz)
+            torch.cuda.synchronize()
+            assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q), (lg, tile, rmax, th)
+            assert torch.equal(dz, dx)
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
 @pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
 @pytest.mark.parametrize("engine", [1, 2])
 def test_blas_every_engine_and_width(gpu, width, engine):
