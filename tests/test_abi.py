@@ -46,3 +46,20 @@ def test_status_strings(libpath):
     assert moma.moma_status_string(0) == "MOMA_OK"
     assert moma.moma_status_string(3) == "MOMA_ERR_SIZE"
     assert moma.moma_status_string(99) == "MOMA_ERR_UNKNOWN"
+
+
+def _enum(name_prefix):
+    """Name -> value of the header's enumerators that start with name_prefix."""
+    src = open(os.path.join(ROOT, "include", "moma.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + name_prefix + r"\w*)\s*=\s*(\d+)", src)}
+
+
+def test_binding_codes_match_header():
+    """The binding's status, operation and word-block codes equal the header's enumerators."""
+    status = _enum("MOMA_ERR_") | _enum("MOMA_OK")
+    assert {v: k for k, v in status.items()} == {k: v for k, v in moma.STATUS.items() if v != "MOMA_ERR_UNKNOWN"}
+    ops = _enum("MOMA_OP_")
+    assert ops == {"MOMA_OP_" + k.upper(): v for k, v in moma.OPS.items()}
+    words = _enum("MOMA_WORD_")
+    assert words == {"MOMA_WORD_" + k.upper(): v for k, v in moma.WORD_OPS.items()}
