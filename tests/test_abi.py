@@ -63,3 +63,13 @@ def test_binding_codes_match_header():
     assert ops == {"MOMA_OP_" + k.upper(): v for k, v in moma.OPS.items()}
     words = _enum("MOMA_WORD_")
     assert words == {"MOMA_WORD_" + k.upper(): v for k, v in moma.WORD_OPS.items()}
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libmoma.so every call raises: there is no CPU fallback path."""
+    monkeypatch.setattr(moma, "_lib", None)
+    monkeypatch.setattr(moma, "LIB_PATH", str(tmp_path / "libmoma.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        moma.lib()
+    with pytest.raises(RuntimeError):
+        moma.moma_status_string(0)
