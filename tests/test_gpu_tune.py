@@ -141,3 +141,31 @@ def test_config_rejects_invalid(gpu):
             gpu.moma_ctx_set_config(ctx, "ntt_fwd", 1 << 10, cta_threads=256, tight_regs=1)
     finally:
         gpu.moma_ctx_destroy(ctx)
+
+
+def test_schedule_table_round_trip(gpu, tmp_path):
+    """Autotuned schedules saved as JSON, loaded and applied to a fresh context: the same effective
+    schedules, and the transform under them still equals the oracle's."""
+    from paper_2501_07535_gb300 import schedules
+    p = inputs.prime(256)
+    ctx = gpu.moma_ctx_create(p.q, 256)
+    ctx2 = gpu.moma_ctx_create(p.q, 256)
+    try:
+        n = 1 << 13
+        t = schedules.Table()
+        best = schedules.tune(t, ctx, 256, "ntt_fwd", n, count=2)
+        schedules.tune(t, ctx, 256, "mul", 4096)
+        path = str(tmp_path / "schedules.json")
+        t.save(path)
+        assert schedules.apply(schedules.Table.load(path), ctx2, 256) == 2
+        assert gpu.moma_ctx_get_config(ctx2, "ntt_fwd", n) == best
+        assert gpu.moma_ctx_get_config(ctx2, "mul", 4096) == gpu.moma_ctx_get_config(ctx, "mul", 4096)
+        x = inputs.residues(p.q, p.L, n, 21)
+        dx = gpu.to_device(x)
+        dy = torch.empty_like(dx)
+        gpu.moma_ntt_fwd(ctx2, n, dx, dy)
+        torch.cuda.synchronize()
+        assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+        gpu.moma_ctx_destroy(ctx2)
