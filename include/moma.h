@@ -76,14 +76,16 @@ moma_status moma_ctx_create(const uint32_t *q, int bits, moma_ctx **out);
 /* Context for a full-width modulus: q odd, with more than bits-32 and at most `bits` bits
  * (the top limb nonzero, up to a modulus that fills the container), else MOMA_ERR_MODULUS.
  * Sec. 5.2 names Montgomery reduction for such moduli, where the 4 spare bits that the
- * Barrett constants of Sec. 3.1 need are absent.  Every product is a word-serial Montgomery
- * product (R = 2^bits, q' = -q^-1 mod 2^32, 2L^2 + L word products); sums form their carry
- * word.  Inputs and outputs are canonical residues as for moma_ctx_create (no Montgomery form
- * visible to the caller: mulmod is two Montgomery products, the second by R^2 mod q;
- * twiddles, the axpy scalar and n^-1 are kept in Montgomery form internally).
- * Every call accepts such a context; the product engine setting is ignored (Montgomery
- * products are carry chains).  In batches their jobs run with the per-call kernels after the
- * persistent launch, like 768-bit jobs. */
+ * Barrett constants of Sec. 3.1 need are absent.  Products by a constant (twiddles, the axpy
+ * scalar, n^-1, kept in Montgomery form internally) are word-serial Montgomery products
+ * (R = 2^bits, q' = -q^-1 mod 2^32, 2L^2 + L word products); the element-wise product of two
+ * vectors (moma_vec_mulmod) is the double-width product reduced by a word-based Barrett
+ * reduction with the (L+1)-limb constant floor(2^(2 bits)/q), or, with engine 4 of
+ * moma_config, two Montgomery products (the second by R^2 mod q); sums form their carry word.
+ * Inputs and outputs are canonical residues as for moma_ctx_create (no Montgomery form is
+ * visible to the caller).  Every call accepts such a context; calls other than
+ * moma_vec_mulmod ignore the product engine setting.  In batches their jobs run with the
+ * per-call kernels after the persistent launch, like 768-bit jobs. */
 moma_status moma_ctx_create_full(const uint32_t *q, int bits, moma_ctx **out);
 
 /* 1 for a context made by moma_ctx_create_full, else 0 (also for NULL). */
@@ -117,7 +119,8 @@ moma_status moma_vec_submod(moma_ctx *ctx, size_t n, const uint32_t *a, const ui
                             uint32_t *c, void *stream);
 
 /* c[i] = a[i] * b[i] mod q by multi-word Barrett reduction (Sec. 3.1 Eq. barrett and
- * Eq. mu; Sec. 3.2 Listing dmulmod generalised to L words). */
+ * Eq. mu; Sec. 3.2 Listing dmulmod generalised to L words); full-width contexts as stated at
+ * moma_ctx_create_full. */
 moma_status moma_vec_mulmod(moma_ctx *ctx, size_t n, const uint32_t *a, const uint32_t *b,
                             uint32_t *c, void *stream);
 
