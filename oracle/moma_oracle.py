@@ -27,6 +27,8 @@ Readings where the paper is silent or inconsistent:
   * Full-width moduli (B = W, Sec. 5.2 names Montgomery reduction for them without detail):
     R = 2^W, REDC taken one 32-bit word at a time with q' = -q^-1 mod 2^32, one final
     conditional subtraction; a product of canonical values is REDC(REDC(a b) (R^2 mod q)).
+    The same product is also reached by Eq. barrett with whole-word shifts and the constant
+    floor(2^(2W) / q) of one word more than q (barrett_full_steps).
 """
 from __future__ import annotations
 
@@ -395,3 +397,23 @@ def mulmod_via_montgomery(a: int, b: int, q: int, width: int) -> int:
     """a b mod q as two Montgomery products: REDC(REDC(a b) (R^2 mod q))."""
     r2 = (1 << (2 * width)) % q
     return montgomery_mul(montgomery_mul(a, b, q, width), r2, q, width)
+
+
+# Eq. barrett for a full-width modulus, with the shifts taken as whole words: base 2^w, q of L
+# words whose top word is nonzero, mu = floor(2^(2Lw) / q) (one word longer than q).
+
+def barrett_full_steps(a: int, b: int, q: int, limbs: int, word_bits: int = 32):
+    """a b mod q by the whole-word Barrett sequence; returns (c, r_before, s).
+
+    t = a b; q1 = t >> (L-1) words; s = (q1 * mu) >> (L+1) words; r = t - s q; q is subtracted
+    while r >= q.  s is floor(t / q) or up to two less, so r_before lies in [0, 3q).
+    """
+    mu = (1 << (2 * limbs * word_bits)) // q
+    t = a * b
+    q1 = t >> ((limbs - 1) * word_bits)
+    s = (q1 * mu) >> ((limbs + 1) * word_bits)
+    r = t - s * q
+    r_before = r
+    while r >= q:
+        r -= q
+    return r, r_before, s

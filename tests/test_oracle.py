@@ -344,6 +344,40 @@ def test_mulmod_via_montgomery_is_the_product(width):
         assert oracle.montgomery_mul(a, b, q, width) == a * b * int(sympy.mod_inverse(1 << width, q)) % q
 
 
+@pytest.mark.parametrize("word_bits,limbs,step", [(3, 2, 1), (4, 2, 7), (3, 3, 23)])
+def test_barrett_full_exhaustive_on_small_words(word_bits, limbs, step):
+    """The whole-word Barrett reading on every a, b < q for odd moduli of `limbs` words of
+    `word_bits` bits with a nonzero top word (every `step`-th such modulus): the exact product,
+    a quotient estimate within 2 below floor(a b / q), hence a value below 3q before the
+    subtractions.  (For a b < q^2 these sizes never show an estimate 2 short: the bound is not
+    tight here.)"""
+    base = 1 << word_bits
+    worst = 0
+    for q in range(base ** (limbs - 1) + 1, base ** limbs, 2 * step):
+        for a in range(q):
+            for b in range(a, q):
+                c, r, s = oracle.barrett_full_steps(a, b, q, limbs, word_bits)
+                Q = a * b // q
+                assert c == a * b % q and Q - 2 <= s <= Q and 0 <= r < 3 * q, (q, a, b)
+                worst = max(worst, Q - s)
+    assert worst >= 1  # the estimate does fall short: the subtractions are needed
+
+
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
+def test_barrett_full_at_machine_words(width):
+    """32-bit words at every container width: moduli with top word 1, 2^W - 1 and the full-width
+    test prime; edge and random operands."""
+    rng = random.Random(width + 17)
+    L = width // 32
+    for q in ((1 << (width - 32)) + 12345, (1 << width) - 1, inputs.prime_full(width).q):
+        edge = [0, 1, q - 1, q - 2, q // 2, (1 << (width - 32)) - 1, (1 << (width - 1)) % q]
+        pairs = [(a, b) for a in edge for b in edge] + [(rng.randrange(q), rng.randrange(q)) for _ in range(200)]
+        for a, b in pairs:
+            c, r, s = oracle.barrett_full_steps(a, b, q, L)
+            Q = a * b // q
+            assert c == a * b % q and Q - 2 <= s <= Q and 0 <= r < 3 * q
+
+
 def test_full_width_transform_roots():
     for w in (64, 128, 256, 384, 512, 768, 1024):
         q = inputs.prime_full(w).q

@@ -162,3 +162,46 @@ def test_planted_montgomery_sign_is_caught():
             caught = True
     assert caught
     assert oracle.montgomery_redc_words(12345, q, W) == 12345 * rinv % q
+
+
+def _barrett_full_pins_hold() -> bool:
+    """test_oracle.py's exhaustive pin of the whole-word Barrett reading, at 3-bit words."""
+    for q in range(9, 64, 2):
+        for a in range(q):
+            for b in range(q):
+                c, r, s = om.barrett_full_steps(a, b, q, 2, 3)
+                Q = a * b // q
+                if c != a * b % q or not (Q - 2 <= s <= Q) or not (0 <= r < 3 * q):
+                    return False
+    return True
+
+
+def _mutant_barrett_full_short_shift(a, b, q, limbs, word_bits=32):
+    # q1 taken from word L instead of word L-1: the estimate loses a word of precision
+    mu = (1 << (2 * limbs * word_bits)) // q
+    t = a * b
+    s = ((t >> (limbs * word_bits)) * mu) >> ((limbs + 1) * word_bits)
+    r = t - s * q
+    r_before = r
+    while r >= q:
+        r -= q
+    return r, r_before, s
+
+
+def _mutant_barrett_full_narrow_mu(a, b, q, limbs, word_bits=32):
+    # mu of L words only (its top word dropped), as if the W-4 bit constant were reused
+    mu = ((1 << (2 * limbs * word_bits)) // q) % (1 << (limbs * word_bits))
+    t = a * b
+    s = ((t >> ((limbs - 1) * word_bits)) * mu) >> ((limbs + 1) * word_bits)
+    r = t - s * q
+    r_before = r
+    while r >= q:
+        r -= q
+    return r, r_before, s
+
+
+@pytest.mark.parametrize("mutant", [_mutant_barrett_full_short_shift, _mutant_barrett_full_narrow_mu])
+def test_planted_full_width_barrett_mistake_is_caught(monkeypatch, mutant):
+    assert _barrett_full_pins_hold()
+    monkeypatch.setattr(om, "barrett_full_steps", mutant)
+    assert not _barrett_full_pins_hold()
