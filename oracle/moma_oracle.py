@@ -113,6 +113,22 @@ def barrett_mulmod_steps(a: int, b: int, q: int, mbits: int, mu: int | None = No
     return c, t_before
 
 
+def barrett_fixed_steps(a: int, w: int, q: int, width: int):
+    """Eq. barrett for a fixed multiplicand w < q, with the quotient constant precomputed for w.
+
+    wp = floor(w 2^W / q) (the companion of w); s = floor(a wp / 2^W) estimates floor(a w / q)
+    to within one below it for any a < 2^W, so r = a w - s q lies in [0, 2q).  Returns
+    (c, r_before, s) with c = a w mod q.
+    """
+    wp = (w << width) // q
+    s = (a * wp) >> width
+    r = a * w - s * q
+    r_before = r
+    while r >= q:
+        r -= q
+    return r, r_before, s
+
+
 # ------------------------------------------------------------------ primes and roots
 
 _SMALL_PRIMES = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61,

@@ -344,6 +344,37 @@ def test_mulmod_via_montgomery_is_the_product(width):
         assert oracle.montgomery_mul(a, b, q, width) == a * b * int(sympy.mod_inverse(1 << width, q)) % q
 
 
+@pytest.mark.parametrize("width,step", [(6, 1), (8, 7)])
+def test_barrett_fixed_exhaustive_on_small_widths(width, step):
+    """The fixed-multiplicand reading on every a < 2^W and w < q for odd q < 2^W (every
+    `step`-th): a w mod q, a quotient estimate at most one below floor(a w / q), hence a value
+    below 2q before the subtractions (the kernels' truncated estimate may take one more)."""
+    worst = 0
+    for q in range(3, 1 << width, 2 * step):
+        for w in range(q):
+            for a in range(1 << width):
+                c, r, s = oracle.barrett_fixed_steps(a, w, q, width)
+                Q = a * w // q
+                assert c == a * w % q and Q - 1 <= s <= Q and 0 <= r < 2 * q, (q, w, a)
+                worst = max(worst, Q - s)
+    assert worst == 1
+
+
+@pytest.mark.parametrize("width", [64, 128, 256, 384, 512, 768, 1024])
+def test_barrett_fixed_at_machine_words(width):
+    """(W-4)-bit test primes, multiplicands w < q (edge and random), operands a over all of
+    [0, 2^W) as in the transforms' lazy values."""
+    rng = random.Random(width + 29)
+    q = inputs.prime(width).q
+    ws = [0, 1, q - 1, q // 2] + [rng.randrange(q) for _ in range(20)]
+    As = [0, 1, q - 1, 4 * q - 1, (1 << width) - 1] + [rng.randrange(1 << width) for _ in range(40)]
+    for w in ws:
+        for a in As:
+            c, r, s = oracle.barrett_fixed_steps(a, w, q, width)
+            Q = a * w // q
+            assert c == a * w % q and Q - 1 <= s <= Q and 0 <= r < 2 * q
+
+
 @pytest.mark.parametrize("word_bits,limbs,step", [(3, 2, 1), (4, 2, 7), (3, 3, 23)])
 def test_barrett_full_exhaustive_on_small_words(word_bits, limbs, step):
     """The whole-word Barrett reading on every a, b < q for odd moduli of `limbs` words of

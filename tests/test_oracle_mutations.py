@@ -205,3 +205,46 @@ def test_planted_full_width_barrett_mistake_is_caught(monkeypatch, mutant):
     assert _barrett_full_pins_hold()
     monkeypatch.setattr(om, "barrett_full_steps", mutant)
     assert not _barrett_full_pins_hold()
+
+
+def _barrett_fixed_pins_hold() -> bool:
+    """test_oracle.py's exhaustive pin of the fixed-multiplicand reading at W = 6."""
+    for q in range(3, 64, 2):
+        for w in range(q):
+            for a in range(64):
+                c, r, s = om.barrett_fixed_steps(a, w, q, 6)
+                Q = a * w // q
+                if c != a * w % q or not (Q - 1 <= s <= Q) or not (0 <= r < 2 * q):
+                    return False
+    return True
+
+
+def _mutant_barrett_fixed_half_companion(a, w, q, width):
+    # companion floor(w 2^(W-1) / q): half the constant, the estimate falls far short
+    wp = (w << (width - 1)) // q
+    s = (a * wp) >> width
+    r = a * w - s * q
+    r_before = r
+    while r >= q:
+        r -= q
+    return r, r_before, s
+
+
+def _mutant_barrett_fixed_rounded_companion(a, w, q, width):
+    # companion rounded up instead of down: the estimate can exceed floor(a w / q)
+    wp = -((-w << width) // q)
+    s = (a * wp) >> width
+    r = a * w - s * q
+    r_before = r
+    while r < 0:
+        r += q
+    while r >= q:
+        r -= q
+    return r, r_before, s
+
+
+@pytest.mark.parametrize("mutant", [_mutant_barrett_fixed_half_companion, _mutant_barrett_fixed_rounded_companion])
+def test_planted_fixed_multiplicand_mistake_is_caught(monkeypatch, mutant):
+    assert _barrett_fixed_pins_hold()
+    monkeypatch.setattr(om, "barrett_fixed_steps", mutant)
+    assert not _barrett_fixed_pins_hold()
