@@ -7,10 +7,12 @@ relies on (through moma_word_probe, raw outputs before any final reduction).
 - the truncated high half: floor(a*b / 2^W) or one less (the Barrett quotient estimate);
 - Barrett reduction (Sec. 3.1 Eq. barrett): the exact residue, and its final correction fires at
   most once (one conditional subtraction suffices for a (W-4)-bit modulus);
-- the fixed-multiplicand product before its corrections: congruent to a*w and below 3q;
+- the fixed-multiplicand product before its corrections: congruent to a*w and below 3q, its
+  quotient estimate the oracle reading's (oracle.barrett_fixed_steps) or one less;
 - the Montgomery product: a*b*R^-1 mod q (full-width contexts);
 - the word-based Barrett reduction of full-width contexts: r = a*b - s*q before its two final
-  subtractions lies in [0, 4q) with s within 3 of floor(a*b/q), and the reduced product is exact,
+  subtractions lies in [0, 4q) with s within 3 of floor(a*b/q) and equal to the oracle reading's
+  estimate (oracle.barrett_full_steps) or one less, and the reduced product is exact,
   for moduli whose top word is 1 (the largest constant floor(2^(2W)/q)) and for 2^W - 1.
 Operands are edge values (0, 1, all-ones words, q - 1, 2^W - 1 where allowed) and seeded draws.
 """
@@ -20,6 +22,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2501_07535_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -104,6 +107,11 @@ def test_word_barrett_one_correction_and_fixed_bound(gpu, width):
             r = _planes(o, 0, L)
             assert all(0 <= v < 3 * q for v in r), engine
             assert all((v - x * w) % q == 0 for v, x in zip(r, aw)), engine
+            # the kernel's quotient estimate is the oracle reading's exact one or one less (its
+            # high half is truncated)
+            for x, v in zip(aw, r):
+                s_or = oracle.barrett_fixed_steps(x, w, q, width)[2]
+                assert (x * w - v) // q in (s_or, s_or - 1), engine
     finally:
         gpu.moma_ctx_destroy(ctx)
 
@@ -149,6 +157,9 @@ def test_word_barrett_full_bound(gpu, width):
                     t = x * y
                     assert 0 <= v < 4 * q and (t - v) % q == 0, (hex(q), engine)
                     assert t // q - 3 <= (t - v) // q <= t // q
+                    # the oracle reading's exact estimate, or one less (truncated high half)
+                    s_or = oracle.barrett_full_steps(x, y, q, L)[2]
+                    assert (t - v) // q in (s_or, s_or - 1), (hex(q), engine)
             with pytest.raises(gpu.MomaError):  # the W-4 bit Barrett block needs a Barrett context
                 _probe(gpu, ctx, "barrett", 1, a[:4], b[:4], L)
         finally:
