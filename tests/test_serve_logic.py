@@ -8,9 +8,10 @@ from paper_2501_07535_gb300 import inputs, serve
 class FakeExecutor:
     """Each batch takes `per_job_s` per job; completion is visible once the host clock passes it."""
 
-    def __init__(self, per_job_s=2e-4, footprint=lambda j: j.n):
+    def __init__(self, per_job_s=2e-4, footprint=lambda j: j.n, clock=time.perf_counter):
         self.per_job = per_job_s
         self.fp = footprint
+        self.clock = clock
         self.launches = []
 
     def start(self, t0):
@@ -20,13 +21,13 @@ class FakeExecutor:
         return self.fp(job)
 
     def launch(self, jobs):
-        now = time.perf_counter() - self.t0
+        now = self.clock() - self.t0
         done = now + self.per_job * len(jobs)
         self.launches.append((now, done, [j.seed for j in jobs]))
         return done
 
     def poll(self, handle):
-        return handle if time.perf_counter() - self.t0 >= handle else None
+        return handle if self.clock() - self.t0 >= handle else None
 
 
 def _jobs(n, size=100):
@@ -135,3 +136,38 @@ def test_class_policy_respects_budget_and_rejects_oversize():
     assert st.rejected == 1 and sched.rejected == [120]
     assert st.completed == 120
     assert st.max_inflight_bytes <= 7000
+
+
+class SimClock:
+    """Simulated time: each reading advances it by a microsecond, a sleep by its length."""
+
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-6
+        return self.t
+
+    def sleep(self, s):
+        self.t += max(s, 1e-6)
+
+
+def test_latency_grows_with_offered_load(monkeypatch):
+    """Two slots of 4-job batches at 1 ms per job serve 2000 jobs/s.  At a quarter of that every
+    job runs almost alone (latency about its own 1 ms); at twice that the queue grows through
+    the stream and the makespan is set by the capacity."""
+    capacity = 2 * 4 / (4 * 1e-3)
+
+    def run(load):
+        clk = SimClock()
+        monkeypatch.setattr(serve.time, "sleep", clk.sleep)
+        ex = FakeExecutor(per_job_s=1e-3, clock=clk)
+        arrivals = [i / (load * capacity) for i in range(400)]
+        sched = serve.Scheduler(ex, budget_bytes=10**9, slots=2, max_batch_jobs=4, clock=clk, idle_sleep_s=1e-5)
+        return sched.run(arrivals, _jobs(400)).summary()
+
+    lo, hi = run(0.25), run(2.0)
+    assert lo["completed"] == hi["completed"] == 400
+    assert lo["p99_ms"] < 2.5 and lo["mean_ms"] < 1.5
+    assert hi["mean_ms"] > 20 * lo["mean_ms"] and hi["p99_ms"] > 20 * lo["p99_ms"]
+    assert 0.9 * capacity < hi["jobs_per_s"] < 1.05 * capacity
