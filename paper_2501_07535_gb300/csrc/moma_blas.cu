@@ -11,8 +11,11 @@ int vec_max_width(int L) { return L <= 8 ? 4 : (L <= 12 ? 2 : 1); }
 
 moma_config vec_config(const moma_ctx* ctx, int vec_op) {
   moma_config c = {0, 0, 0, 0, 0, 0};
-  auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
-  if (it != ctx->configs.end()) c = it->second;
+  {
+    std::lock_guard<std::mutex> g(ctx->lock);  // moma_ctx_set_config may write the map meanwhile
+    auto it = ctx->configs.find(std::make_pair(MOMA_OP_ADD + vec_op, -1));
+    if (it != ctx->configs.end()) c = it->second;
+  }
   // Karatsuba (engine 3) measured at or above schoolbook for mulmod on GB300 from 64 to 768 bits
   // (1.00x at 256 bits up to 1.2x at 768 bits; 0.9x at 1024 bits, where carry chains are kept);
   // carry chains for the other ops

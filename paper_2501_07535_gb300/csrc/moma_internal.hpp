@@ -62,7 +62,7 @@ struct moma_ctx {
   moma::BigU Q;
   moma::Reducer* red = nullptr;  // host reductions mod q
   // transform state, filled on first use
-  std::mutex lock;
+  mutable std::mutex lock;  // guards plans, configs and the transform state
   int ntt_ready = 0;  // 0: not yet, 1: ok, -1: modulus not prime
   uint32_t g = 0;     // smallest quadratic non-residue
   int two_adicity = 0;

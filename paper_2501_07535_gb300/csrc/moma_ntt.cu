@@ -65,14 +65,21 @@ int max_tile_log(int L) {
 
 moma_config ntt_config(const moma_ctx* ctx, int op, int logn) {
   moma_config c = {0, 0, 0, 0, 0, 0};
-  auto it = ctx->configs.find(std::make_pair(op, logn));
-  if (it != ctx->configs.end()) c = it->second;
+  bool set = false;
+  {
+    std::lock_guard<std::mutex> g(ctx->lock);  // moma_ctx_set_config may write the map meanwhile
+    auto it = ctx->configs.find(std::make_pair(op, logn));
+    if (it != ctx->configs.end()) {
+      c = it->second;
+      set = true;
+    }
+  }
   const NttDefaults d = ntt_defaults(ctx->L);
   if (c.engine == 0) c.engine = d.engine;
   if (c.tile_log == 0) c.tile_log = d.tile_log;
   if (c.max_logr == 0) c.max_logr = c.tile_log == d.tile_log ? d.max_logr : (c.tile_log > 6 ? c.tile_log - 5 : 1);
   if (c.cta_threads == 0) c.cta_threads = d.threads;
-  if (it == ctx->configs.end() && c.cta_threads <= 128) c.tight_regs = d.tight;
+  if (!set && c.cta_threads <= 128) c.tight_regs = d.tight;
   c.vec_width = 0;
   return c;
 }

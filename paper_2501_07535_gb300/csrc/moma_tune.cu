@@ -48,12 +48,10 @@ extern "C" moma_status moma_ctx_get_config(moma_ctx* ctx, int op, size_t n, moma
   if (is_ntt_op(op)) {
     const int lg = log2_of(n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-    std::lock_guard<std::mutex> g(ctx->lock);
-    *cfg = ntt_config(ctx, op, lg);
+    *cfg = ntt_config(ctx, op, lg);  // takes the context's lock for the lookup
     return MOMA_OK;
   }
   if (is_vec_op(op)) {
-    std::lock_guard<std::mutex> g(ctx->lock);
     *cfg = vec_config(ctx, op - MOMA_OP_ADD);
     return MOMA_OK;
   }
@@ -167,10 +165,8 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   if (rc) return rc;
   rc = moma_ctx_set_config(ctx, op, n, &best_c);
   if (rc) return rc;
-  if (best) {  // the effective schedule, defaults filled in (as moma_ctx_get_config reports it)
-    std::lock_guard<std::mutex> g(ctx->lock);
+  if (best)  // the effective schedule, defaults filled in (as moma_ctx_get_config reports it)
     *best = lg >= 0 ? ntt_config(ctx, op, lg) : vec_config(ctx, op - MOMA_OP_ADD);
-  }
   if (best_us) *best_us = best_t;
   return MOMA_OK;
 }
