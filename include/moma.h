@@ -32,9 +32,10 @@
  *   asynchronous: the return code reports argument, configuration and launch errors
  *   only.  Errors raised on the device (a bounded wait that ran out) are recorded in
  *   the context and returned by moma_ctx_sync_status().
- * Threads.  A context may be used from several host threads; plan creation is
- *   serialised inside the context.  Calls that overlap on the device and write the same
- *   buffers race, as with any CUDA kernel.
+ * Threads.  A context may be used from several host threads; plan creation and the
+ *   schedule table (moma_ctx_set_config, and the lookups every call makes) are serialised
+ *   inside the context.  Calls that overlap on the device and write the same buffers race,
+ *   as with any CUDA kernel.
  */
 #ifndef MOMA_H
 #define MOMA_H
