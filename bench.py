@@ -36,9 +36,9 @@ VEC_N = 1 << 24
 L = WIDTH // 32
 
 
-# DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20)
-# from profiles/ntt_pass_kernel_L8_n2p20.md (8-transform capture x 2), valid for this schedule
-# and kernel version (None otherwise).
+# DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20):
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a pass over 8 transforms, x 2;
+# valid for this schedule and kernel version (None otherwise).
 NTT_PASS_TRAFFIC_BYTES = 962_203_648
 NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 2, "tile_log": 10, "max_logr": 5, "cta_threads": 128, "tight_regs": 0}
 
@@ -196,6 +196,14 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def bench_config(world=1):
+    """The workload the line's value is quoted on (shared by both arms)."""
+    return {"workload": f"forward cyclic NTT, n=2^{LOGN}, 256-bit container (252-bit prime), {NTT_BATCH} transforms "
+                        f"per step", "n": 1 << LOGN, "bits": WIDTH, "limbs": L, "batch": NTT_BATCH,
+            "l2": "inputs larger than L2 (512 MiB per NTT step, 1.5 GiB per mulmod step)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -243,6 +251,7 @@ def run_ours(args):
     moma.moma_ntt_fwd_many(ctx, n, NTT_BATCH, dx, dy)
     torch.cuda.synchronize()
     ntt_cfg = moma.moma_ctx_get_config(ctx, "ntt_fwd", n)
+    mul_cfg = moma.moma_ctx_get_config(ctx, "mul", VEC_N)
     n_pass_launches = _pass_count(ntt_cfg, LOGN)
 
     # ---- integer-multiply peak (same run, same GPU): the fastest word-product form measured
@@ -254,6 +263,7 @@ def run_ours(args):
     probe_peak = max(probe.values())  # word products / s, fastest form measured in this run
     sm_max_mhz = _measured_peaks().get("sm_max_mhz") or 2070.0
     prod_peak = product_peak(sms, sm_max_mhz)  # unit-count peak at the max SM clock
+    hbm = _measured_peaks().get("hbm_gbs")
 
     # ---- NTT region
     def ntt_step():
@@ -296,15 +306,21 @@ def run_ours(args):
     clocks = clk.summary()
     e2e = world * NTT_BATCH * args.steps / (e2e_ms * 1e-3)
     step_bytes = NTT_BATCH * L * n * 4
+    del xs, dx, dy, a, b, c
+    torch.cuda.empty_cache()
 
     # ---- roofline
-    hbm = _measured_peaks().get("hbm_gbs")
     roof = ntt_roofline(n, L, NTT_BATCH, ntt_ms * 1e-3 / args.steps, prod_peak)
     mul_roof = vec_roofline(L, VEC_N, mul_ms * 1e-3 / args.steps, hbm, prod_peak)
     launches = args.steps * n_pass_launches  # pass kernels in the timed NTT region
+
+    # ---- the other workloads (bulky tables first in the line, the headline block last)
+    sens = run_sensitivity()
+    c3 = run_c3_sweep(prod_peak) if not args.quick else None
+    c2 = run_c2_table(hbm, prod_peak) if not args.quick else None
+    c1 = run_c1_latency()
     c4 = run_uneven_batch(max(3, args.steps // 2), 2)
     c5 = run_served(n_jobs=args.serve_jobs) if args.serve_jobs > 0 else None
-    sens = run_sensitivity()
 
     result = {
         "metric": METRIC,
@@ -319,11 +335,20 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic: seeded uniform residues mod a seed-generated 252-bit prime q = c*2^32+1",
-        "config": {"workload": f"forward cyclic NTT, n=2^{LOGN}, 256-bit container (252-bit prime), "
-                               f"{NTT_BATCH} transforms per step; mulmod on 2^24 elements, same prime",
-                   "n": n, "bits": WIDTH, "limbs": L, "batch": NTT_BATCH, "vec_n": VEC_N,
-                   "l2": "inputs larger than L2 (512 MiB per NTT step, 1.5 GiB per mulmod step)",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(world),
+        "sensitivity": sens,
+        "c3_ntt_sweep": c3,
+        "c2_blas": c2,
+        "c1_single_ntt": c1,
+        "batched_vs_plain": c4,
+        "served": c5,
+        "multiply_probe": {"wide_t_products_per_s": round(probe[5] / 1e12, 3),
+                           "carry_chain_t_products_per_s": round(probe[0] / 1e12, 3), "sms": sms},
+        "schedule": {"ntt_fwd": ntt_cfg, "mul": mul_cfg},
+        "e2e": {"value": round(e2e, 2), "unit": "NTT/s", "h2d_bytes_per_step": step_bytes,
+                "d2h_bytes_per_step": step_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
         "roofline": {**roof,
                      "traffic": NTT_PASS_TRAFFIC_BYTES if all(ntt_cfg.get(k) == v for k, v in
                                                               NTT_PASS_TRAFFIC_SCHEDULE.items()) else None,
@@ -332,20 +357,9 @@ def run_ours(args):
                      "peak_probe": round(probe_peak / 1e12, 3),
                      "frac_of_probe": round(roof["achieved"] / (probe_peak / 1e12), 4),
                      "algorithmic": f"(n/2)log2(n) mulmods x (2L^2+L) = {word_products_per_mulmod(L)} word "
-                                    f"products per mulmod, {NTT_BATCH} transforms per step"},
-        "mulmod": {"value": round(gelem, 3), "unit": "Gelem/s", "ms_per_step": round(mul_ms / args.steps, 4),
-                   "gpu_launches": args.steps,
-                   "roofline": mul_roof},
-        "batched_vs_plain": c4,
-        "served": c5,
-        "sensitivity": sens,
-        "e2e": {"value": round(e2e, 2), "unit": "NTT/s", "h2d_bytes_per_step": step_bytes,
-                "d2h_bytes_per_step": step_bytes},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "multiply_probe": {"wide_t_products_per_s": round(probe[5] / 1e12, 3),
-                           "carry_chain_t_products_per_s": round(probe[0] / 1e12, 3), "sms": sms},
-        "schedule": ntt_cfg,
+                                    f"products per mulmod, {NTT_BATCH} transforms per step",
+                     "mulmod": {"gelem_s": round(gelem, 3), "n": VEC_N, "bits": WIDTH,
+                                "ms_per_step": round(mul_ms / args.steps, 4), **mul_roof}},
     }
     if pool is not None:
         rate, wall = oracle_ntt_rate(pool, cores, q)
@@ -356,10 +370,30 @@ def run_ours(args):
                                             f"({wall:.1f} s wall)",
                                   "mulmod": {"value": round(mrate, 6), "unit": "Gelem/s",
                                              "sample": f"{cores} x 2^19-element mulmod ({mwall:.1f} s wall)"}}
+    result["headline"] = headline(result)
     if rank == 0:
         print(json.dumps(result), flush=True)
     moma.moma_ctx_destroy(ctx)
     replicas.finalize()
+
+
+def headline(r):
+    """The four parts of the metric in one short block, printed last in the line."""
+    m = r["roofline"]["mulmod"]
+    h = {"ntt_per_s": r["value"], "ntt_roofline_frac": r["roofline"]["frac"], "e2e_ntt_per_s": r["e2e"]["value"],
+         "mulmod_gelem_s": m["gelem_s"], "mulmod_roofline_frac": m["frac"]}
+    if r.get("batched_vs_plain"):
+        h["batched_over_plain"] = r["batched_vs_plain"]["speedup"]
+    s = r.get("served")
+    if s:
+        h.update({"served_over_plain": s["served_over_plain"], "served_p50_ms": s["p50_ms"],
+                  "served_p99_ms_median": s["p99_ms_median"], "served_p99_ms_max": s["p99_ms_max"],
+                  "served_p99_ms_runs": s["open_loop"]["p99_ms_runs"]})
+    if r.get("c1_single_ntt"):
+        h["c1_latency_us"] = r["c1_single_ntt"]["us_per_call"]
+    if r.get("cpu_baseline"):
+        h["cpu_oracle_ntt_per_s"] = r["cpu_baseline"]["value"]
+    return h
 
 
 # Each step's transforms are copied in, transformed and copied out in E2E_CHUNKS chunks that rotate
@@ -489,6 +523,148 @@ def _pass_count(cfg, logn):
     return math.ceil(logn / cfg["max_logr"])
 
 
+def _timer(steps):
+    """Mean milliseconds of fn() over `steps` calls after one untimed call (CUDA events)."""
+    import torch
+
+    def timed(fn, warm=1):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+    return timed
+
+
+C2_WIDTHS = (128, 256, 384, 768)
+C2_OPS = ("add", "sub", "mul", "axpy")
+
+
+def run_c2_table(hbm_gbs, prod_peak, steps=5, n=VEC_N):
+    """The element-wise BLAS workload: addmod, submod, mulmod and axpy on 2^24 seeded residues at
+    128/256/384/768 bits (each context's default schedule).  Per cell: time per call, Gelem/s,
+    achieved HBM GB/s and word products/s, and the roofline fraction (the slower of 12L bytes per
+    element at the HBM peak and, for mul and axpy, 2L^2 + L word products at the product peak).
+    Inputs (1.5 to 4.8 GiB per call) are larger than L2.  `steps` timed calls per cell after one
+    warm-up call."""
+    import torch
+
+    from paper_2501_07535_gb300 import inputs, moma
+    timed = _timer(steps)
+    rows = []
+    for w in C2_WIDTHS:
+        p = inputs.prime(w)
+        ctx = moma.moma_ctx_create(p.q, w)
+        a = moma.to_device(inputs.residues(p.q, p.L, n, 1))
+        b = moma.to_device(inputs.residues(p.q, p.L, n, 2))
+        c = torch.empty_like(a)
+        alpha = inputs.scalar_residue(p.q, 3)
+        calls = {"add": lambda: moma.moma_vec_addmod(ctx, n, a, b, c),
+                 "sub": lambda: moma.moma_vec_submod(ctx, n, a, b, c),
+                 "mul": lambda: moma.moma_vec_mulmod(ctx, n, a, b, c),
+                 "axpy": lambda: moma.moma_vec_axpymod(ctx, n, alpha, a, b, c)}
+        for op in C2_OPS:
+            ms = timed(calls[op])
+            r = vec_roofline(p.L, n, ms * 1e-3, hbm_gbs, prod_peak, products=op in ("mul", "axpy"))
+            cfg = moma.moma_ctx_get_config(ctx, op, n)
+            rows.append({"bits": w, "op": op, "us": r["achieved_us"], "gelem_s": round(n / ms / 1e6, 2),
+                         "gbs": r["hbm_gbs_achieved"], "t_products_s": r["products_t_achieved"], "bound": r["bound"],
+                         "roofline_us": r["time_us"], "frac": r["frac"],
+                         "schedule": [cfg["engine"], cfg["vec_width"], cfg["tile_log"]]})
+        assert moma.moma_ctx_sync_status(ctx) == 0
+        moma.moma_ctx_destroy(ctx)
+        del a, b, c
+        torch.cuda.empty_cache()
+    return {"n": n, "steps": steps, "schedule_fields": ["engine", "vec_width", "staged_tile_log"], "rows": rows}
+
+
+C3_LOGN = tuple(range(14, 25))
+C3_WIDTHS = (256, 384)
+C3_BATCHES = (1, 2, 4, 8, 16)
+
+
+def run_c3_sweep(prod_peak, steps=2):
+    """The plain transform sweep: forward then inverse NTT, n = 2^14..2^24 at 256 and 384 bits,
+    batch 1..16, every transform a separate call (moma_ntt_fwd / moma_ntt_inv, the default
+    schedule).  One seeded transform per (n, width), copied into every batch slot on the device
+    (identical work per slot).  Per cell: milliseconds per step (b forward + b inverse calls),
+    transforms per second (forward and inverse each counted) and the fraction of the unit-count
+    product peak ((n/2) log2 n mulmods of 2L^2 + L word products per transform).  `steps` timed
+    steps per cell after one warm-up step; the round trip is checked once per (n, width)."""
+    import torch
+
+    from paper_2501_07535_gb300 import inputs, moma
+    timed = _timer(steps)
+    rows = []
+    for w in C3_WIDTHS:
+        p = inputs.prime(w)
+        ctx = moma.moma_ctx_create(p.q, w)
+        cap = max(C3_BATCHES) * p.L << max(C3_LOGN)
+        fin = torch.empty(cap, dtype=torch.int32, device="cuda")
+        fout = torch.empty_like(fin)
+        for lg in C3_LOGN:
+            n = 1 << lg
+            bmax = max(C3_BATCHES)
+            din = fin[:bmax * p.L * n].view(bmax, p.L, n)
+            dout = fout[:bmax * p.L * n].view(bmax, p.L, n)
+            din.copy_(moma.to_device(inputs.residues(p.q, p.L, n, seed=lg + w)).unsqueeze(0).expand(bmax, -1, -1))
+            moma.moma_ntt_fwd(ctx, n, din[0], dout[0])
+            moma.moma_ntt_inv(ctx, n, dout[0], dout[0])
+            torch.cuda.synchronize()
+            ok = bool(torch.equal(dout[0], din[0]))
+            for bsz in C3_BATCHES:
+                def step():
+                    for t in range(bsz):
+                        moma.moma_ntt_fwd(ctx, n, din[t], dout[t])
+                    for t in range(bsz):
+                        moma.moma_ntt_inv(ctx, n, dout[t], dout[t])
+                ms = timed(step)
+                roof = ntt_roofline(n, p.L, 2 * bsz, ms * 1e-3, prod_peak)
+                rows.append([lg, w, bsz, round(ms, 4), round(2 * bsz / ms * 1e3, 1), roof["frac"], ok])
+        assert moma.moma_ctx_sync_status(ctx) == 0
+        moma.moma_ctx_destroy(ctx)
+        del fin, fout, din, dout
+        torch.cuda.empty_cache()
+    return {"steps": steps, "fields": ["log2_n", "bits", "batch", "ms_per_step", "transforms_per_s", "frac",
+                                       "round_trip_exact"], "rows": rows}
+
+
+def run_c1_latency(calls=200):
+    """The single small transform: one forward cyclic NTT of 2^12 points at 256 bits, issued as
+    `calls` back-to-back calls on one stream; microseconds per call (launch and kernel), and the
+    same calls captured once in a CUDA graph and replayed."""
+    import torch
+
+    from paper_2501_07535_gb300 import inputs, moma
+    p = inputs.prime(256)
+    n = 1 << 12
+    ctx = moma.moma_ctx_create(p.q, 256)
+    x = moma.to_device(inputs.residues(p.q, p.L, n, 0))
+    y = torch.empty_like(x)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        f = lambda: moma.moma_ntt_fwd(ctx, n, x, y, st)  # noqa: E731
+        ms = _timer(calls)(f, warm=5)
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                for _ in range(20):
+                    f()
+            gms = _timer(max(1, calls // 20))(g.replay, warm=2)
+        except RuntimeError:
+            gms = None
+    st.synchronize()
+    assert moma.moma_ctx_sync_status(ctx) == 0
+    moma.moma_ctx_destroy(ctx)
+    return {"n": n, "bits": 256, "calls": calls, "us_per_call": round(ms * 1e3, 2),
+            "graph_us_per_call": round(gms * 1e3 / 20, 2) if gms is not None else None}
+
+
 def run_uneven_batch(steps, warmup, n_jobs=256, seed=0):
     """The uneven batched workload: n_jobs transforms / cyclic products, n = 2^10..2^20 log-uniform,
     widths 128/256/384; one persistent launch (graph replay) against the same jobs as per-call launches."""
@@ -539,8 +715,8 @@ def run_uneven_batch(steps, warmup, n_jobs=256, seed=0):
 
 
 def run_sensitivity(steps=5):
-    """Sec. 5.4 analogues: (1) forward NTT runtime against width at n = 4096 from 64 to 1024 bits
-    (batches of 256, ns per butterfly = 2t/(n log2 n) as in Sec. 5.3), with the slowdown per
+    """Sec. 5.4 analogues on seeded residues: (1) forward NTT runtime against width at n = 4096 from
+    64 to 1024 bits (batches of 256, ns per butterfly = 2t/(n log2 n) as in Sec. 5.3), with the slowdown per
     doubling of the width as the paper reports it; (2) mulmod with schoolbook carry chains,
     whole mad.wide products and Karatsuba (Eq. mulk) at each width, 2^22 elements; (3) the same
     mulmod and transform over a full-width modulus: mulmod by the word-based Barrett reduction and
@@ -567,8 +743,7 @@ def run_sensitivity(steps=5):
         p = inputs.prime(w)
         ctx = moma.moma_ctx_create(p.q, w)
         n, cnt = 4096, 256
-        x = torch.zeros((cnt, p.L, n), dtype=torch.int32, device="cuda")
-        x[:, 0, :] = 3  # canonical
+        x = moma.to_device(inputs.residues(p.q, p.L, n * cnt, 40 + w).reshape(p.L, cnt, n).transpose(1, 0, 2).copy())
         y = torch.empty_like(x)
         ms = timed(lambda: moma.moma_ntt_fwd_many(ctx, n, cnt, x, y))
         ns_bfly = ms * 1e6 / cnt * 2 / (n * 12)
@@ -596,8 +771,7 @@ def run_sensitivity(steps=5):
         full_gelem = vn / timed(lambda: moma.moma_vec_mulmod(fctx, vn, fa, fb, c)) / 1e6
         moma.moma_ctx_set_config(fctx, "mul", vn, engine=4)
         mont_gelem = vn / timed(lambda: moma.moma_vec_mulmod(fctx, vn, fa, fb, c)) / 1e6
-        fx = torch.zeros_like(x)
-        fx[:, 0, :] = 3
+        fx = moma.to_device(inputs.residues(pf.q, pf.L, n * cnt, 50 + w).reshape(pf.L, cnt, n).transpose(1, 0, 2).copy())
         fms = timed(lambda: moma.moma_ntt_fwd_many(fctx, n, cnt, fx, y))
         out["full_width_montgomery"].append({
             "bits": w, "mulmod_gelem_s": round(full_gelem, 2),
@@ -615,13 +789,18 @@ def run_sensitivity(steps=5):
     return out
 
 
-def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
+def median_run(runs):
+    """The run whose p99 is the median of the runs' p99 (the lower middle one for an even count)."""
+    return sorted(runs, key=lambda r: r["p99_ms"])[(len(runs) - 1) // 2]
+
+
+def run_served(n_jobs=10000, seed=0, load=0.8, slots=4, repeats=3):
     """The served stream: Poisson arrivals of n_jobs transforms (2^12..2^22) and mulmod/axpy
     vectors (2^16..2^24) at 256/384/768 bits, continuous batching under a 40 GB budget, with
     size-class micro-batches (serve.Scheduler policy "class").  Capacity is measured closed-loop
-    (all requests present at t = 0); the open-loop runs offer load x capacity, twice under each
-    policy (size classes, plain FIFO micro-batches), alternating; the lower-p99 run of each is
-    reported with both runs' p99 beside it; one more run each at 0.5 and 1.0 x capacity gives the
+    (all requests present at t = 0); the open-loop runs offer load x capacity, `repeats` times under
+    each policy (size classes, plain FIFO micro-batches), alternating; the median-p99 run of each is
+    reported with every run's p99 beside it; one more run each at 0.5 and 1.0 x capacity gives the
     latency against the offered load.  The same jobs as plain per-call launches give the per-call
     throughput."""
     import torch
@@ -636,14 +815,14 @@ def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
         capacity = closed["jobs_per_s"]
         rate = load * capacity
         arrivals = [a / rate for a in unit_arrivals]
-        # open loop: the two policies alternate twice on the same arrivals; the median run of each
-        # (by p99) is reported, the spread beside it
+        # open loop: the two policies alternate `repeats` times on the same arrivals; the run with the
+        # median p99 of each policy is reported, every run's p99 beside it
         runs = {"class": [], "fifo": []}
-        for _ in range(2):
+        for _ in range(repeats):
             for pol in ("class", "fifo"):
                 runs[pol].append(serve.serve(arrivals, jobs, ctxs, slots=slots, executor=ex, policy=pol).summary())
         torch.cuda.synchronize()
-        opened, fifo = (sorted(runs[pol], key=lambda r: r["p99_ms"])[0] for pol in ("class", "fifo"))
+        opened, fifo = (median_run(runs[pol]) for pol in ("class", "fifo"))
         opened["p99_ms_runs"] = [r["p99_ms"] for r in runs["class"]]
         fifo["p99_ms_runs"] = [r["p99_ms"] for r in runs["fifo"]]
         # the same arrivals at half and at full capacity (size classes, one run each)
@@ -661,7 +840,9 @@ def run_served(n_jobs=10000, seed=0, load=0.8, slots=4):
                 "served_over_plain": round(capacity / (n_jobs / plain_s), 3), "offered_load": load,
                 "offered_jobs_per_s": round(rate, 1), "closed_loop": closed, "open_loop": opened,
                 "open_loop_fifo": fifo, "load_sweep": sweep, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"],
-                "budget_gb": 40, "slots": slots}
+                "p99_ms_median": opened["p99_ms"], "p99_ms_min": min(opened["p99_ms_runs"]),
+                "p99_ms_max": max(opened["p99_ms_runs"]), "budget_gb": 40, "slots": slots,
+                "resident_gb": round(ex.resident_bytes() / 1e9, 3)}
     finally:
         ctxs.close()
 
@@ -697,10 +878,10 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall / args.steps * 1e3, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "python-int",
            "data": "synthetic: seeded uniform residues mod a seed-generated 252-bit prime",
-           "config": {"workload": f"forward cyclic NTT, n=2^{LOGN}, 256-bit container (252-bit prime), "
-                                  f"one transform per host core per step", "n": 1 << LOGN, "bits": WIDTH},
+           "config": bench_config(world),
            "cpu_baseline": {"value": round(rate, 4), "unit": "NTT/s", "cores": cores, "kind": "oracle",
-                            "sample": f"{cores} full 2^{LOGN}-point NTTs per step (warm-up steps at 2^{LOGN - 4})"},
+                            "sample": f"{cores} full 2^{LOGN}-point forward NTTs per step, one per host core "
+                                      f"(warm-up steps at 2^{LOGN - 4})"},
            "e2e": {"value": round(rate, 4), "unit": "NTT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -718,6 +899,7 @@ def main():
                     choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "mont_mul_redc", "batch",
                              "batch_large"])
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
+    ap.add_argument("--quick", action="store_true", help="skip the BLAS table and the transform sweep")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -99,6 +99,13 @@ void moma_ctx_destroy(moma_ctx *ctx);
 /* Number of 32-bit limbs L of the context (0 for NULL). */
 int moma_ctx_limbs(const moma_ctx *ctx);
 
+/* Bytes of device memory the context holds right now: the twiddle tables of every
+ * transform plan built so far (one per size, direction and schedule; about n entries of
+ * 2L words per direction) and its status word.  Scratch buffers of calls in flight are not
+ * included (they come from the stream-ordered pool and are released by the calls).  For
+ * admission control by memory budget.  0 for NULL. */
+size_t moma_ctx_device_bytes(const moma_ctx *ctx);
+
 /* Write the primitive n-th root of unity w_n the transforms use (L host limbs):
  * w_n = g^((q-1)/n) with g the smallest integer >= 2 that is a quadratic non-residue
  * mod q (the paper leaves the choice of root open, Sec. 2.3).  n a power of two
@@ -108,6 +115,18 @@ moma_status moma_ctx_root(moma_ctx *ctx, size_t n, uint32_t *w_out);
 /* Block until all work the context issued is done and return (then clear) the first
  * device-side error recorded since the last call (MOMA_ERR_TIMEOUT), else MOMA_OK. */
 moma_status moma_ctx_sync_status(moma_ctx *ctx);
+
+/* Bound, in nanoseconds of GPU global time, of every wait of this context's staged BLAS
+ * kernels on a shared-memory stage filled by bulk copies (default 2e9).  A wait that runs
+ * out records MOMA_ERR_TIMEOUT (see moma_ctx_sync_status); the kernel waits, bounded again,
+ * for its copies still in flight and returns, so it never hangs.  ns 0 is MOMA_ERR_INVALID_ARG. */
+moma_status moma_ctx_set_wait_limit(moma_ctx *ctx, uint64_t ns);
+
+/* Test hook: the next staged BLAS launch of this context arms its first CTA's first stage
+ * for 16 bytes more than its copies deliver, so that one wait runs out (the copies themselves
+ * complete normally).  That launch's results are undefined; moma_ctx_sync_status then
+ * reports MOMA_ERR_TIMEOUT. */
+moma_status moma_ctx_inject_missing_copy(moma_ctx *ctx);
 
 /* ------------------------------------------------------------------ modular BLAS */
 
@@ -177,22 +196,26 @@ moma_status moma_polymul_negacyclic(moma_ctx *ctx, size_t n, const uint32_t *a, 
                                     uint32_t *c, void *stream);
 
 /* Same result as moma_ntt_fwd (one transform), but the call allocates no device memory:
- * its intermediate buffers are a fixed 8 MiB array inside the library, held by every GPU
- * that loads it until the process exits.  Meant for callers that may not allocate device
- * memory at call time (memory owned by another allocator under a fixed budget, or a hot
- * path that must not wait on an allocator).  The paper has no counterpart; this is an
- * interface convenience of this library.
+ * its intermediate buffers are a fixed 8 MiB array inside the library.  The array is placed
+ * on a GPU when the first context on that GPU is created (moma_ctx_create or
+ * moma_ctx_create_full, which look up its device address then) and stays there until the
+ * process exits.  Meant for callers that may not allocate device memory at call time (memory
+ * owned by another allocator under a fixed budget, or a hot path that must not wait on an
+ * allocator).  The paper has no counterpart; this is an interface convenience of this
+ * library.
  * Limits and conditions:
  *   - L*n <= 2^20 words (n <= 2^19 at 64 bits, 2^18 at 128, 2^17 at 256, 2^16 at 384); larger
  *     n gives MOMA_ERR_SIZE.  Contexts of 512 bits and up give MOMA_ERR_UNSUPPORTED.
- *   - The size's twiddle tables must already exist: call moma_ntt_fwd once with this
- *     context and n beforehand (that call allocates); otherwise MOMA_ERR_INVALID_ARG.
- *   - The context's device must be current.  The first call on a device looks up the
- *     array's device address (no allocation); make that first call before any stream
- *     capture that should contain this entry point.
+ *     Full-width contexts (moma_ctx_create_full) up to 384 bits are accepted.
+ *   - The size's twiddle tables must already exist for the forward schedule in effect: call
+ *     moma_ntt_fwd once with this context and n beforehand (that call allocates), and again
+ *     after any moma_ctx_set_config, moma_autotune or loaded schedule that changes the
+ *     forward schedule for this n; otherwise MOMA_ERR_INVALID_ARG.
+ *   - The context's device must be current.
  *   - All calls share the one array.  Each call writes every word it later reads, so
  *     nothing needs clearing between calls, but calls that overlap on the GPU (other
- *     streams, other host threads, other contexts) race on it and give wrong results. */
+ *     streams, other host threads, other contexts) race on it and give wrong results.
+ *     out == in is allowed. */
 moma_status moma_ntt_fwd_noalloc(moma_ctx *ctx, size_t n, const uint32_t *in, uint32_t *out,
                                  void *stream);
 
@@ -280,6 +303,13 @@ typedef enum {
  *              1 and 2 compute the same schoolbook sums (Sec. 2.2 Eq. muls, Table 1 mulqdd);
  *              all engines give identical results.
  *   tile_log   transforms: log2 of the elements one CTA holds in shared memory.
+ *              BLAS: 0 = operands read with direct vector loads; the width's staged tile
+ *              (10 up to 128 bits, 9 at 256 bits, 8 at 384 bits) = operands staged in shared
+ *              memory by asynchronous bulk copies (the TMA engine, cp.async.bulk) in tiles of
+ *              2^tile_log elements, three tiles in flight per CTA (needs n a multiple of 4 and
+ *              16-byte aligned operands, else direct loads); other values are invalid.
+ *              Contexts of 512 bits and up and full-width contexts always load directly
+ *              (tile_log must be 0 there). 
  *   max_logr   transforms: largest radix (log2) of one Stockham pass.
  *   vec_width  BLAS: elements per thread per step (1, 2 or 4; limited by alignment; full-width
  *              contexts always take 1).

@@ -36,6 +36,9 @@ class Contexts:
             self._h[key] = moma.moma_ctx_create(inputs.prime(width, prime_seed).q, width)
         return self._h[key]
 
+    def handles(self) -> list[int]:
+        return list(self._h.values())
+
     def close(self):
         for h in self._h.values():
             moma.moma_ctx_destroy(h)
@@ -43,8 +46,12 @@ class Contexts:
 
 
 class JobSet:
-    def __init__(self, jobs, contexts: Contexts | None = None, device="cuda"):
-        self.jobs = list(jobs)
+    """The jobs of one rank: with world_size > 1 the set keeps only its cost-balanced share
+    (replicas.shard_balanced), so N ranks on N GPUs together run the whole list once."""
+
+    def __init__(self, jobs, contexts: Contexts | None = None, device="cuda", rank: int = 0, world_size: int = 1):
+        from . import replicas
+        self.jobs = replicas.shard_balanced(jobs, rank, world_size, replicas.job_cost)
         self.ctx = contexts or Contexts()
         self.a, self.b, self.out, self.alpha, self.host_a, self.host_b = [], [], [], [], [], []
         for j in self.jobs:

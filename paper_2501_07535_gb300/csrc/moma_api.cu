@@ -90,6 +90,14 @@ static moma_status ctx_create(const uint32_t* q, int bits, bool mont, moma_ctx**
     delete c;
     return MOMA_ERR_OOM;
   }
+  // the fixed scratch array of moma_ntt_fwd_noalloc is placed on this device now (module load),
+  // not in that entry point's first call
+  if (noalloc_prepare(c->device) != MOMA_OK) {
+    cudaFree(c->d_status);
+    delete c->red;
+    delete c;
+    return MOMA_ERR_CUDA;
+  }
   cudaMemset(c->d_status, 0, sizeof(int));
   *out = c;
   return MOMA_OK;
@@ -114,6 +122,14 @@ void moma_ctx_destroy(moma_ctx* ctx) {
 }
 
 int moma_ctx_limbs(const moma_ctx* ctx) { return ctx ? ctx->L : 0; }
+
+size_t moma_ctx_device_bytes(const moma_ctx* ctx) {
+  if (!ctx) return 0;
+  std::lock_guard<std::mutex> g(ctx->lock);
+  size_t b = sizeof(int);  // the status word
+  for (const auto& kv : ctx->plans) b += kv.second->table_bytes;
+  return b;
+}
 
 static int log2_exact(size_t n) {
   if (n == 0 || (n & (n - 1))) return -1;
@@ -140,6 +156,18 @@ moma_status moma_ctx_sync_status(moma_ctx* ctx) {
   if (cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MOMA_ERR_CUDA;
   if (v) cudaMemset(ctx->d_status, 0, sizeof(int));
   return (moma_status)v;
+}
+
+moma_status moma_ctx_set_wait_limit(moma_ctx* ctx, uint64_t ns) {
+  if (!ctx || ns == 0) return MOMA_ERR_INVALID_ARG;
+  ctx->wait_ns = ns;
+  return MOMA_OK;
+}
+
+moma_status moma_ctx_inject_missing_copy(moma_ctx* ctx) {
+  if (!ctx) return MOMA_ERR_INVALID_ARG;
+  ctx->inject_missing_copy.store(1);
+  return MOMA_OK;
 }
 
 static bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }

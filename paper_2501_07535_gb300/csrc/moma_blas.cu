@@ -9,6 +9,19 @@ namespace moma {
 // Largest vector width per L: keeps the two operand tiles (2*V*L words) near 64 registers.
 int vec_max_width(int L) { return L <= 8 ? 4 : (L <= 12 ? 2 : 1); }
 
+int vec_max_log_tile(int L) {
+  switch (L) {
+    case 2: return vec_staged_max_log_tile<2>();
+    case 4: return vec_staged_max_log_tile<4>();
+    case 8: return vec_staged_max_log_tile<8>();
+    case 12: return vec_staged_max_log_tile<12>();
+    case 16: return vec_staged_max_log_tile<16>();
+    case 24: return vec_staged_max_log_tile<24>();
+    case 32: return vec_staged_max_log_tile<32>();
+  }
+  return 0;
+}
+
 moma_config vec_config(const moma_ctx* ctx, int vec_op) {
   moma_config c = {0, 0, 0, 0, 0, 0};
   {
@@ -27,7 +40,9 @@ moma_config vec_config(const moma_ctx* ctx, int vec_op) {
     const int pref = ctx->L <= 4 ? 4 : (vec_op == VEC_MUL ? 1 : 2);
     c.vec_width = pref < vm ? pref : vm;
   }
-  c.tile_log = 0;
+  // tile_log: 0 = direct vector loads; 8..10 = operands staged by bulk copies in tiles of
+  // 2^tile_log elements (full-width contexts always load directly)
+  if (ctx->mont) c.tile_log = 0;
   c.max_logr = 0;
   return c;
 }

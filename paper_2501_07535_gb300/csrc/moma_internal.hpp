@@ -46,6 +46,7 @@ struct Plan {
   uint32_t* psi = nullptr;  // negacyclic: [n][2L] psi^e (forward) or n^-1 psi^-e (inverse)
   std::vector<PassDesc> passes;
   uint32_t* d_tables = nullptr;  // one allocation holding every table of the plan
+  size_t table_bytes = 0;         // its size
   uint32_t scale[kMaxL] = {}, scalep[kMaxL] = {};  // n^-1 and its companion (inverse)
   int tile_log = 0;                                // log2 of the CTA tile (elements)
 };
@@ -71,6 +72,10 @@ struct moma_ctx {
   // schedule per (op, logn) for transforms, (op, -1) for BLAS; absent = defaults
   std::map<std::pair<int, int>, moma_config> configs;
   int* d_status = nullptr;  // device-side error word
+  // bound of one wait of the staged BLAS kernels on a shared-memory stage (ns of global time)
+  uint64_t wait_ns = 2000000000ull;
+  // test hook: the next staged BLAS launch makes one wait run out (moma_ctx_inject_missing_copy)
+  std::atomic<int> inject_missing_copy{0};
 };
 
 namespace moma {
@@ -81,6 +86,7 @@ inline moma_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MOMA_O
 // moma_blas.cu
 enum VecOp { VEC_ADD = 0, VEC_SUB = 1, VEC_MUL = 2, VEC_AXPY = 3 };
 int vec_max_width(int L);
+int vec_max_log_tile(int L);  // largest staged tile (log2 elements) for L limbs, 0 if none
 moma_config vec_config(const moma_ctx* ctx, int vec_op);  // effective (defaults filled)
 moma_status launch_vec(moma_ctx* ctx, int op, size_t n, const uint32_t* a, const uint32_t* b,
                        uint32_t* c, const uint32_t* alpha_host, cudaStream_t st);
@@ -122,10 +128,9 @@ moma_status run_words_wide(moma_ctx* ctx, int op, int engine, size_t n, const ui
                            uint32_t* out, cudaStream_t st);
 // Existing plan or null; never builds one (no allocation).
 Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr);
-// All passes of an existing single-transform plan with caller-provided scratch
-// (s1: passes 0, 2, ...; s2: passes 1, 3, ...; each L*n words; unused ones may be null).
-moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out,
-                             const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st);
+// moma_noalloc.cu: look up the device address of the fixed scratch array on device `dev`
+// (current), once per device; called when a context is created.
+moma_status noalloc_prepare(int dev);
 BigU root_of_unity(moma_ctx* ctx, int logn);  // requires ntt_prepare()
 
 // Shoup-style companion floor(w * 2^(32L) / q) for a host constant w < q.

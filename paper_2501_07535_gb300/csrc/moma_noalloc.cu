@@ -23,9 +23,11 @@ std::mutex g_noalloc_lock;
 uint32_t* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
-// Device address of the array on the current device (host code only sees a stand-in
-// symbol).  Resolved once per device, the first time this device is used here.
-static moma_status noalloc_scratch(int dev, uint32_t** out) {
+// Device address of the array on device `dev`, which must be current (host code only sees a
+// stand-in symbol).  Looked up once per device, when the first context on that device is
+// created: with lazy module loading the driver loads this file's module, and places the array,
+// at that first look-up, so it happens in a call that is allowed to allocate.
+moma_status noalloc_prepare(int dev) {
   if (dev < 0 || dev >= kMaxDevices) return MOMA_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(g_noalloc_lock);
   if (!g_noalloc_addr[dev]) {
@@ -33,8 +35,13 @@ static moma_status noalloc_scratch(int dev, uint32_t** out) {
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MOMA_ERR_CUDA;
     g_noalloc_addr[dev] = static_cast<uint32_t*>(p);
   }
-  *out = g_noalloc_addr[dev];
   return MOMA_OK;
+}
+
+static uint32_t* noalloc_scratch(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> g(g_noalloc_lock);
+  return g_noalloc_addr[dev];
 }
 
 }  // namespace moma
@@ -57,8 +64,7 @@ extern "C" moma_status moma_ntt_fwd_noalloc(moma_ctx* ctx, size_t n, const uint3
   const moma_config cfg = ntt_config(ctx, MOMA_OP_NTT_FWD, lg);
   Plan* pl = find_plan(ctx, lg, false, cfg.tile_log, cfg.max_logr);
   if (!pl) return MOMA_ERR_INVALID_ARG;  // twiddle tables not built yet: call moma_ntt_fwd once
-  uint32_t* scratch = nullptr;
-  moma_status rc = noalloc_scratch(dev, &scratch);
-  if (rc) return rc;
-  return run_plan_scratch(ctx, pl, in, out, cfg, scratch, scratch + kNoAllocWords, (cudaStream_t)stream);
+  uint32_t* scratch = noalloc_scratch(dev);  // resolved when the context was created
+  if (!scratch) return MOMA_ERR_CUDA;
+  return run_plan_buffers(ctx, pl, 1, in, nullptr, out, cfg, scratch, scratch + kNoAllocWords, (cudaStream_t)stream);
 }

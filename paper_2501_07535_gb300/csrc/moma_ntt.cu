@@ -193,6 +193,7 @@ static moma_status build_plan(moma_ctx* ctx, int logn, bool inverse, int tile_lo
     delete pl;
     return MOMA_ERR_OOM;
   }
+  pl->table_bytes = words * 4;
   uint32_t* ptr = pl->d_tables;
   const uint64_t n = 1ull << logn;
   for (auto& d : pl->passes) {
@@ -321,20 +322,6 @@ Plan* find_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_log
   std::lock_guard<std::mutex> g(ctx->lock);
   auto it = ctx->plans.find(std::make_tuple(logn, inverse ? 1 : 0, tile_log, max_logr, 0));
   return it == ctx->plans.end() ? nullptr : it->second;
-}
-
-moma_status run_plan_scratch(moma_ctx* ctx, const Plan* pl, const uint32_t* in, uint32_t* out,
-                             const moma_config& cfg, uint32_t* s1, uint32_t* s2, cudaStream_t st) {
-  const size_t P = pl->passes.size();
-  moma_status rc = MOMA_OK;
-  const uint32_t* src = in;
-  for (size_t i = 0; i < P && rc == MOMA_OK; ++i) {
-    uint32_t* dst = (i + 1 == P) ? out : ((i % 2 == 0) ? s1 : s2);
-    const uint32_t flags = ((i == 0 && pl->inverse) ? F_SCALE : 0) | ((i + 1 == P) ? F_LAST : 0);
-    rc = run_pass_l(ctx, pl, pl->passes[i], 1, src, nullptr, dst, flags, cfg, st);
-    src = dst;
-  }
-  return rc;
 }
 
 moma_status launch_ntt_cfg(moma_ctx* ctx, int logn, size_t count, bool inverse, const uint32_t* in, uint32_t* out,

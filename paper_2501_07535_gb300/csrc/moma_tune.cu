@@ -36,6 +36,7 @@ extern "C" moma_status moma_ctx_set_config(moma_ctx* ctx, int op, size_t n, cons
     if (cfg->engine == 4 && !(ctx->mont && op == MOMA_OP_MUL)) return MOMA_ERR_INVALID_ARG;
     if (cfg->vec_width != 0 && cfg->vec_width != 1 && cfg->vec_width != 2 && cfg->vec_width != 4)
       return MOMA_ERR_INVALID_ARG;
+    if (cfg->tile_log != 0 && cfg->tile_log != vec_max_log_tile(ctx->L)) return MOMA_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->lock);
     ctx->configs[std::make_pair(op, -1)] = *cfg;
     return MOMA_OK;
@@ -111,8 +112,12 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
     // full-width contexts: one element per thread, and mulmod's engine 4 (two Montgomery products)
     const int engines = op == MOMA_OP_MUL ? (ctx->mont ? 4 : 3) : (op == MOMA_OP_AXPY && !ctx->mont ? 2 : 1);
     const int vmax = ctx->mont ? 1 : vec_max_width(ctx->L);
-    for (int engine = 1; engine <= engines; ++engine)
+    const int tmax = ctx->mont ? 0 : vec_max_log_tile(ctx->L);
+    for (int engine = 1; engine <= engines; ++engine) {
       for (int v = 1; v <= vmax; v *= 2) cands.push_back({engine, 0, 0, v, 0, 0});
+      // staged by bulk copies in the width's tile (the vector width does not apply)
+      if (tmax) cands.push_back({engine, tmax, 0, 1, 0, 0});
+    }
   } else {
     return MOMA_ERR_INVALID_ARG;
   }

@@ -24,7 +24,8 @@ import numpy as np
 
 WIDTHS = (64, 128, 256, 384, 512, 768, 1024)
 _HERE = os.path.dirname(os.path.abspath(__file__))
-PRIMES_JSON = os.path.join(os.path.dirname(_HERE), "tests", "golden", "primes.json")
+# the seed-generated moduli (input data, not results), written by tests/golden/make_primes.py
+PRIMES_JSON = os.path.join(_HERE, "primes.json")
 
 
 def limbs_of(width_bits: int) -> int:

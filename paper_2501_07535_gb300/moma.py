@@ -44,8 +44,11 @@ _SIGS = {
     "moma_ctx_is_full": (ctypes.c_int, [_P]),
     "moma_ctx_destroy": (None, [_P]),
     "moma_ctx_limbs": (ctypes.c_int, [_P]),
+    "moma_ctx_device_bytes": (ctypes.c_size_t, [_P]),
     "moma_ctx_root": (ctypes.c_int, [_P, _SZ, _P]),
     "moma_ctx_sync_status": (ctypes.c_int, [_P]),
+    "moma_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "moma_ctx_inject_missing_copy": (ctypes.c_int, [_P]),
     "moma_vec_addmod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
     "moma_vec_submod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
     "moma_vec_mulmod": (ctypes.c_int, [_P, _SZ, _P, _P, _P, _P]),
@@ -174,6 +177,10 @@ def moma_ctx_limbs(ctx: int) -> int:
     return lib().moma_ctx_limbs(ctx)
 
 
+def moma_ctx_device_bytes(ctx: int) -> int:
+    return lib().moma_ctx_device_bytes(ctx)
+
+
 def moma_ctx_root(ctx: int, n: int) -> int:
     L = moma_ctx_limbs(ctx)
     out = (ctypes.c_uint32 * L)()
@@ -183,6 +190,14 @@ def moma_ctx_root(ctx: int, n: int) -> int:
 
 def moma_ctx_sync_status(ctx: int) -> int:
     return lib().moma_ctx_sync_status(ctx)
+
+
+def moma_ctx_set_wait_limit(ctx: int, ns: int):
+    _check(lib().moma_ctx_set_wait_limit(ctx, ns), "moma_ctx_set_wait_limit")
+
+
+def moma_ctx_inject_missing_copy(ctx: int):
+    _check(lib().moma_ctx_inject_missing_copy(ctx), "moma_ctx_inject_missing_copy")
 
 
 def moma_vec_addmod(ctx, n, a, b, c, stream=None):

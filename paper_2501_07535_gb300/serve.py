@@ -2,13 +2,16 @@
 
 Requests arrive over time (a seeded Poisson stream).  The scheduler keeps a FIFO of
 arrived jobs and, whenever a slot is free, admits jobs from the head of the queue as long as
-their device memory (operands, output, transform scratch) fits the HBM budget, and launches
-them together as one persistent batch on one of several streams.  Micro-batches admitted while
-others are still on the GPU run concurrently with them; a finished batch frees its slot and its
-budget, and the next admission round takes the jobs that arrived meanwhile.  Twiddle tables and
-operands stay resident on the device across jobs (one context per modulus; inputs come from a
-per-(modulus, size) device cache).  Latency of a job = its batch's device completion time
-minus its arrival time.
+their device memory (operands, output, transform scratch) fits the HBM budget together with
+everything the server keeps resident, and launches them together as one persistent batch on one
+of several streams.  Micro-batches admitted while others are still on the GPU run concurrently
+with them; a finished batch frees its slot and its memory, and the next admission round takes
+the jobs that arrived meanwhile.  Resident across jobs, and charged to the same budget: the
+twiddle tables of every transform plan (one context per modulus) and one seeded operand master
+per (modulus, operand).  Each admitted job gets its own operand buffers, filled on its stream from
+the masters (the request's data arriving on the device), and an output buffer; they are released
+when its batch completes.  Latency of a job = its batch's device completion time minus its
+arrival time.
 
 `Scheduler` is the host logic only (no CUDA), driven by an executor with launch/poll/footprint;
 `GpuExecutor` is the CUDA one.  `serve()` runs a stream and returns throughput and latency
@@ -44,6 +47,8 @@ class ServeStats:
     batches: int = 0
     max_inflight_bytes: int = 0
     max_concurrent_batches: int = 0
+    resident_bytes: int = 0
+    deferred_for_memory: int = 0
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_s) if self.latencies_s else np.zeros(1)
@@ -54,11 +59,19 @@ class ServeStats:
                 "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                 "mean_ms": round(float(lat.mean()) * 1e3, 3), "batches": self.batches,
                 "max_concurrent_batches": self.max_concurrent_batches,
-                "max_inflight_gb": round(self.max_inflight_bytes / 1e9, 3)}
+                "max_inflight_gb": round(self.max_inflight_bytes / 1e9, 3),
+                "resident_gb": round(self.resident_bytes / 1e9, 3),
+                "max_total_gb": round((self.resident_bytes + self.max_inflight_bytes) / 1e9, 3),
+                "deferred_for_memory": self.deferred_for_memory}
 
 
 class Scheduler:
     """Admission by memory budget, a fixed number of concurrent micro-batches.
+
+    The budget covers what the executor keeps resident (`executor.resident_bytes()`, if it has
+    one: tables, operand masters) plus the footprint of every job in flight; a job that does not
+    fit waits until batches complete, and a job that could never fit beside the resident memory
+    is refused.
 
     policy "fifo": a micro-batch takes jobs from the head of the queue in arrival order.
     policy "class": the head of the queue opens the micro-batch and fixes its size class (small or
@@ -89,8 +102,13 @@ class Scheduler:
         f = getattr(self.ex, "cost", None)
         return f(job) if f else 0.0
 
-    def _take_class(self, queue, jobs, used, rejected):
-        """One size-homogeneous micro-batch from the queue (policy "class")."""
+    def _resident(self) -> int:
+        f = getattr(self.ex, "resident_bytes", None)
+        return int(f()) if f else 0
+
+    def _take_class(self, queue, jobs, used, rejected, avail):
+        """One size-homogeneous micro-batch from the queue (policy "class"); `avail` is the budget
+        left beside the resident memory."""
         batch, nbytes, cost = [], 0, 0.0
         skipped = []
         cls = None
@@ -100,18 +118,19 @@ class Scheduler:
             j = queue.popleft()
             scanned += 1
             need = self.ex.footprint(jobs[j])
-            if need > self.budget:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+            if need > avail:  # can never fit: refuse it (MOMA_ERR_BUDGET)
                 rejected.append(j)
                 continue
             c = self._cost(jobs[j])
             large = c >= self.large_cost
             if cls is None:  # the head of the queue opens the batch
-                if used + need > self.budget:
+                if used + need > avail:
                     skipped.append(j)
+                    self._deferred += 1
                     break
                 cls = large
                 cap = max(cap, c)
-            elif large != cls or cost + c > cap or used + nbytes + need > self.budget:
+            elif large != cls or cost + c > cap or used + nbytes + need > avail:
                 skipped.append(j)
                 continue
             batch.append(j)
@@ -129,6 +148,7 @@ class Scheduler:
         rejected = []
         used = 0
         stats = ServeStats(n_jobs=n, completed=0, rejected=0, makespan_s=0.0, latencies_s=[])
+        self._deferred = 0
         t0 = self.clock()
         self.ex.start(t0)
         nxt = 0
@@ -149,19 +169,24 @@ class Scheduler:
                 used -= f.nbytes
                 progressed = True
             inflight = keep
+            resident = self._resident()
+            stats.resident_bytes = max(stats.resident_bytes, resident)
+            avail = self.budget - resident
             while queue and len(inflight) < self.slots:
                 if self.policy == "class":
-                    batch, nbytes = self._take_class(queue, jobs, used, rejected)
+                    batch, nbytes = self._take_class(queue, jobs, used, rejected, avail)
                 else:
                     batch, nbytes = [], 0
                     while queue and len(batch) < self.max_batch:
                         j = queue[0]
                         need = self.ex.footprint(jobs[j])
-                        if need > self.budget:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+                        if need > avail:  # can never fit: refuse it (MOMA_ERR_BUDGET)
                             rejected.append(j)
                             queue.popleft()
                             continue
-                        if used + nbytes + need > self.budget:
+                        if used + nbytes + need > avail:
+                            if not batch:
+                                self._deferred += 1
                             break
                         batch.append(j)
                         nbytes += need
@@ -183,6 +208,7 @@ class Scheduler:
                 else:
                     time.sleep(self.idle_sleep)
         finished = [j for j in range(n) if done[j] is not None]
+        stats.deferred_for_memory = self._deferred
         stats.completed = len(finished)
         stats.rejected = len(rejected)
         stats.latencies_s = [done[j] - arrivals[j] for j in finished]
@@ -205,11 +231,11 @@ class GpuExecutor:
         self.keep = keep_outputs
         self.master_log = master_log
         self._masters = {}
-        self._inputs = {}
         self.outputs = {}
 
-    # -- device-resident operands: one seeded master per (modulus, operand); larger inputs
-    #    repeat it, smaller ones are a prefix of each limb plane (still uniform residues)
+    # -- resident operand masters: one seeded master per (modulus, operand); a job's operand is a
+    #    fresh buffer filled from it (larger inputs repeat it, smaller ones take a prefix of each
+    #    limb plane: still uniform residues)
     def _master(self, width, prime_seed, which):
         key = (width, prime_seed, which)
         if key not in self._masters:
@@ -218,18 +244,21 @@ class GpuExecutor:
                 inputs.residues(p.q, p.L, 1 << self.master_log, 900 + 10 * prime_seed + which + width))
         return self._masters[key]
 
-    def operand(self, job, which):
-        key = (job.width, job.prime_seed, job.n, which)
-        t = self._inputs.get(key)
-        if t is None:
-            m = self._master(job.width, job.prime_seed, which)
-            N = m.shape[1]
+    def operand(self, job, which, stream=None):
+        """A new device buffer with the job's operand `which`, filled on `stream` (default: the
+        current stream)."""
+        torch = self.torch
+        m = self._master(job.width, job.prime_seed, which)
+        N = m.shape[1]
+        with torch.cuda.stream(stream or torch.cuda.current_stream()):
             if job.n <= N:
-                t = m[:, :job.n].contiguous()
-            else:
-                t = m.repeat(1, job.n // N).contiguous()
-            self._inputs[key] = t
-        return t
+                return m[:, :job.n].contiguous()
+            return m.repeat(1, job.n // N)
+
+    def resident_bytes(self) -> int:
+        """Device memory kept across jobs: the operand masters and every context's tables."""
+        masters = sum(t.numel() * 4 for t in self._masters.values())
+        return masters + sum(self.moma.moma_ctx_device_bytes(h) for h in self.ctx.handles())
 
     def cost(self, job) -> float:
         """Rough GPU seconds of one job (scheduling only): transforms scale as n log2 n L^2 from a
@@ -242,6 +271,8 @@ class GpuExecutor:
         return 0.45e-3 * r * job.n / (1 << 24)
 
     def footprint(self, job) -> int:
+        """Device bytes a job holds while in flight: its operand and output buffers and, for
+        transforms, the intermediate buffers of its passes."""
         L = job.width // 32
         vec = 4 * L * job.n
         if job.op in ("ntt_fwd", "ntt_inv"):
@@ -251,12 +282,12 @@ class GpuExecutor:
         return vec * 3
 
     def prewarm(self, jobs):
-        """Build every transform plan (twiddle tables) and operand the stream will use."""
+        """Build every operand master and transform plan (twiddle tables) the stream will use."""
         seen = set()
         for j in jobs:
-            self.operand(j, 0)
+            self._master(j.width, j.prime_seed, 0)
             if j.op not in ("ntt_fwd", "ntt_inv"):
-                self.operand(j, 1)
+                self._master(j.width, j.prime_seed, 1)
             key = (j.width, j.prime_seed, j.n, j.op)
             if j.op in ("ntt_fwd", "ntt_inv", "polymul") and key not in seen:
                 seen.add(key)
@@ -264,7 +295,9 @@ class GpuExecutor:
                 out = self.torch.empty_like(x)
                 c = self.ctx.get(j.width, j.prime_seed)
                 (self.moma.moma_ntt_fwd if j.op == "ntt_fwd" else self.moma.moma_ntt_inv)(c, j.n, x, out)
+                del x, out
         self.torch.cuda.synchronize()
+        self.torch.cuda.empty_cache()
 
     def start(self, t0):
         self.base = self.torch.cuda.Event(enable_timing=True)
@@ -277,13 +310,14 @@ class GpuExecutor:
         torch, moma = self.torch, self.moma
         sid = self.free_streams.pop(0)
         st = self.streams[sid]
-        dicts, outs = [], []
+        dicts, outs, held = [], [], []
         for j in jobs:
-            a = self.operand(j, 0)
-            b = self.operand(j, 1) if j.op not in ("ntt_fwd", "ntt_inv") else None
+            a = self.operand(j, 0, st)
+            b = self.operand(j, 1, st) if j.op not in ("ntt_fwd", "ntt_inv") else None
             with torch.cuda.stream(st):
                 out = torch.empty_like(a)
             outs.append(out)
+            held += [a, b]
             alpha = inputs.scalar_residue(inputs.prime(j.width, j.prime_seed).q, j.seed) if j.op == "axpy" else None
             dicts.append({"op": j.op, "ctx": self.ctx.get(j.width, j.prime_seed), "n": j.n, "a": a, "b": b,
                           "out": out, "alpha": alpha})
@@ -294,7 +328,7 @@ class GpuExecutor:
         if self.keep:
             for j, o in zip(jobs, outs):
                 self.outputs[j.seed] = o
-        return {"batch": h, "event": ev, "stream": sid, "outs": outs}
+        return {"batch": h, "event": ev, "stream": sid, "outs": outs, "held": held}
 
     def poll(self, handle):
         if not handle["event"].query():
@@ -306,33 +340,31 @@ class GpuExecutor:
 
 def run_plain(jobs, executor, stream=None):
     """The same jobs as plain per-call launches (one library call per job, arrival order, one
-    stream, all present at t = 0), on the executor's resident operands.  Returns the seconds from
-    the first launch to the end of the last job (CUDA events)."""
+    stream, all present at t = 0), each job's operands filled from the executor's resident masters
+    as in the served form.  Returns the seconds from the first launch to the end of the last job
+    (CUDA events)."""
     import torch
 
     from . import moma
     ctx = executor.ctx
-    outs = {}
     st = stream or torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(st):
         e0.record(st)
-        for j in jobs:
-            a = executor.operand(j, 0)
-            key = (j.width, j.n)
-            if key not in outs:
-                outs[key] = torch.empty_like(a)
-            o = outs[key]
+        for j in jobs:  # each job's operands filled from the masters, as in the served form
+            a = executor.operand(j, 0, st)
+            o = torch.empty_like(a)
             c = ctx.get(j.width, j.prime_seed)
             if j.op == "ntt_fwd":
                 moma.moma_ntt_fwd(c, j.n, a, o, st)
             elif j.op == "ntt_inv":
                 moma.moma_ntt_inv(c, j.n, a, o, st)
             elif j.op == "mul":
-                moma.moma_vec_mulmod(c, j.n, a, executor.operand(j, 1), o, st)
+                moma.moma_vec_mulmod(c, j.n, a, executor.operand(j, 1, st), o, st)
             else:
                 al = inputs.scalar_residue(inputs.prime(j.width, j.prime_seed).q, j.seed)
-                moma.moma_vec_axpymod(c, j.n, al, a, executor.operand(j, 1), o, st)
+                moma.moma_vec_axpymod(c, j.n, al, a, executor.operand(j, 1, st), o, st)
+            del a, o
         e1.record(st)
     e1.synchronize()
     return e0.elapsed_time(e1) * 1e-3
@@ -344,8 +376,20 @@ def served_jobs(n_jobs=10000, seed=0, rate_per_s=1000.0):
     return inputs.served_stream(n_jobs=n_jobs, seed=seed, rate_per_s=rate_per_s)
 
 
+def rank_share(arrivals, jobs, rank: int = 0, world_size: int = 1):
+    """The requests one rank serves when N ranks (one per GPU) share a stream: round-robin by arrival
+    order, as a front end dispatching requests in turn would (disjoint, together complete)."""
+    if world_size <= 1:
+        return list(arrivals), list(jobs)
+    order = sorted(range(len(jobs)), key=lambda i: arrivals[i])
+    mine = sorted(order[rank::world_size])
+    return [arrivals[i] for i in mine], [jobs[i] for i in mine]
+
+
 def serve(arrivals, jobs, contexts, slots=4, budget_bytes=BUDGET_BYTES, max_batch_jobs=64, executor=None,
-          policy="fifo"):
+          policy="fifo", rank: int = 0, world_size: int = 1):
+    """Serve the stream (or, with world_size > 1, this rank's share of it) and return its ServeStats."""
+    arrivals, jobs = rank_share(arrivals, jobs, rank, world_size)
     ex = executor or GpuExecutor(contexts, slots=slots)
     sched = Scheduler(ex, budget_bytes=budget_bytes, slots=slots, max_batch_jobs=max_batch_jobs, policy=policy)
     return sched.run(arrivals, jobs)

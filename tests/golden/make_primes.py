@@ -1,9 +1,13 @@
-"""Writes tests/golden/primes.json: seed-generated NTT-friendly primes per width.
+"""Writes paper_2501_07535_gb300/primes.json: seed-generated NTT-friendly primes per width.
+
+The table is input data for the library's users (moduli of the benchmark and test workloads);
+it is kept in the package so that the library does not depend on the test directory.
 
 Two tables: moduli of W-4 bits (Barrett contexts) and full-width moduli of W bits
 (Montgomery contexts).  Calls only the oracle (gen_prime, gen_prime_full, two_adicity).
 Run from the repository root:
-    python tests/golden/make_primes.py
+    python tests/golden/make_primes.py           (write the table)
+    python tests/golden/make_primes.py --check   (exit 1 if the committed table differs)
 """
 import json
 import os
@@ -16,7 +20,11 @@ WIDTHS = (64, 128, 256, 384, 512, 768, 1024)
 SEEDS = (0, 1, 2, 3)
 
 
-def main():
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+TABLE = os.path.join(ROOT, "paper_2501_07535_gb300", "primes.json")
+
+
+def table():
     out = {"comment": "q = c*2^32 + 1 with exactly W-4 bits (paper Sec. 5.2); c from "
                       "random.Random('moma:<W>:<seed>'); Miller-Rabin accepted; written by "
                       "tests/golden/make_primes.py from oracle.gen_prime",
@@ -34,11 +42,18 @@ def main():
             q = gen_prime_full(w, s)
             out["full_primes"].append({"width": w, "seed": s, "q": hex(q), "bits": q.bit_length(),
                                        "two_adicity": two_adicity(q)})
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "primes.json")
-    with open(path, "w") as f:
-        json.dump(out, f, indent=1)
-        f.write("\n")
+    return json.dumps(out, indent=1) + "\n"
+
+
+def main(argv):
+    text = table()
+    if "--check" in argv:
+        with open(TABLE) as f:
+            return 0 if f.read() == text else 1
+    with open(TABLE, "w") as f:
+        f.write(text)
+    return 0
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main(sys.argv[1:]))

@@ -166,3 +166,105 @@ def test_ctx_rejects_bad_moduli(gpu):
         assert lib.moma_ctx_create(ctypes.cast(arr, ctypes.c_void_p), bits, ctypes.byref(h)) == 2  # MODULUS
     arr = (ctypes.c_uint32 * 8)(*inputs.int_to_limbs(inputs.prime(256).q, 8))
     assert lib.moma_ctx_create(ctypes.cast(arr, ctypes.c_void_p), 200, ctypes.byref(h)) == 1
+
+
+STAGED_TILES = {64: (10,), 128: (10,), 256: (9,), 384: (8,)}
+
+
+@pytest.mark.parametrize("width", [64, 128, 256, 384])
+@pytest.mark.parametrize("op", OPS)
+def test_blas_staged_parity(gpu, width, op):
+    """Operands staged in shared memory by bulk copies: every tile size and product engine, sizes
+    with several tiles per CTA and a ragged tail past the last whole tile (n a multiple of 4, so
+    the staged path is taken), against the oracle."""
+    p = inputs.prime(width)
+    q, L = p.q, p.L
+    ctx = gpu.moma_ctx_create(q, width)
+    engines = {"mul": (1, 2, 3), "axpy": (1, 2)}.get(op, (1,))
+    try:
+        alpha = inputs.scalar_residue(q, seed=5)
+        for tile in STAGED_TILES[width]:
+            for eng in engines:
+                gpu.moma_ctx_set_config(ctx, op, 1 << 20, engine=eng, tile_log=tile)
+                cfg = gpu.moma_ctx_get_config(ctx, op, 1 << 20)
+                assert (cfg["engine"], cfg["tile_log"]) == (eng, tile)
+                # the largest size gives every CTA of the persistent grid more tiles than stages
+                for n, seed in ((4, 1), (1 << tile, 2), (3 * (1 << tile) + 4, 3), (3 * (1 << 20) + 1028, 4)):
+                    a = inputs.residues(q, L, n, seed)
+                    b = inputs.residues(q, L, n, seed + 50)
+                    da, db = gpu.to_device(a), gpu.to_device(b)
+                    dc = torch.empty_like(da)
+                    _run(gpu, ctx, op, n, da, db, dc, alpha)
+                    torch.cuda.synchronize()
+                    if n < 1 << 16:
+                        got = inputs.to_ints(gpu.to_host(dc))
+                        ref = _ref(op, inputs.to_ints(a), inputs.to_ints(b), q, alpha)
+                    else:  # a seeded sample, the first tiles and the ragged end
+                        rng = np.random.Generator(np.random.PCG64(n + tile))
+                        idx = np.unique(np.concatenate([rng.integers(0, n, 3000), np.arange(2048),
+                                                        np.arange(n - 3000, n)]))
+                        got = inputs.to_ints(gpu.to_host(dc[:, torch.from_numpy(idx).cuda()]))
+                        ref = _ref(op, inputs.sample_ints(a, idx), inputs.sample_ints(b, idx), q, alpha)
+                    assert got == ref, (width, op, tile, eng, n)
+        assert gpu.moma_ctx_sync_status(ctx) == 0
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
+def test_blas_staged_fallback_and_inplace(gpu):
+    """A staged schedule with operands that cannot be bulk-copied (planes not 16-byte aligned, n not
+    a multiple of 4) takes the direct loads; in-place calls (c == a, out == y) stay exact."""
+    p = inputs.prime(256)
+    q, L = p.q, p.L
+    ctx = gpu.moma_ctx_create(q, 256)
+    try:
+        gpu.moma_ctx_set_config(ctx, "mul", 1, engine=3, tile_log=9)
+        gpu.moma_ctx_set_config(ctx, "axpy", 1, engine=2, tile_log=9)
+        for n, off in ((4099, 0), (4096, 1), (8192, 0)):
+            a = inputs.residues(q, L, n, 11)
+            b = inputs.residues(q, L, n, 12)
+            buf_a = torch.zeros(L * n + off, dtype=torch.int32, device="cuda")
+            buf_b = torch.zeros(L * n + off, dtype=torch.int32, device="cuda")
+            va, vb = buf_a[off:].view(L, n), buf_b[off:].view(L, n)
+            va.copy_(gpu.to_device(a))
+            vb.copy_(gpu.to_device(b))
+            gpu.moma_vec_mulmod(ctx, n, va, vb, va)
+            torch.cuda.synchronize()
+            ab = oracle.vec_mulmod(inputs.to_ints(a), inputs.to_ints(b), q)
+            assert inputs.to_ints(gpu.to_host(va)) == ab, (n, off)
+            alpha = inputs.scalar_residue(q, 13)
+            gpu.moma_vec_axpymod(ctx, n, alpha, vb, va, va)
+            torch.cuda.synchronize()
+            assert inputs.to_ints(gpu.to_host(va)) == oracle.vec_axpy(alpha, inputs.to_ints(b), ab, q), (n, off)
+        assert gpu.moma_ctx_sync_status(ctx) == 0
+    finally:
+        gpu.moma_ctx_destroy(ctx)
+
+
+def test_blas_staged_wait_runs_out(gpu):
+    """The bounded wait of the staged kernel: the test hook arms one stage for 16 bytes that never
+    arrive, the wait gives up after the (short) limit, the status reports MOMA_ERR_TIMEOUT, the
+    kernel ends, and the next launch is exact again."""
+    p = inputs.prime(256)
+    q, L = p.q, p.L
+    n = 1 << 20
+    ctx = gpu.moma_ctx_create(q, 256)
+    try:
+        gpu.moma_ctx_set_config(ctx, "mul", n, engine=3, tile_log=9)
+        gpu.moma_ctx_set_wait_limit(ctx, 2_000_000)  # 2 ms
+        a = inputs.residues(q, L, n, 21)
+        b = inputs.residues(q, L, n, 22)
+        da, db = gpu.to_device(a), gpu.to_device(b)
+        dc = torch.empty_like(da)
+        gpu.moma_ctx_inject_missing_copy(ctx)
+        gpu.moma_vec_mulmod(ctx, n, da, db, dc)
+        assert gpu.moma_ctx_sync_status(ctx) == 7  # MOMA_ERR_TIMEOUT
+        assert gpu.moma_ctx_sync_status(ctx) == 0  # cleared
+        gpu.moma_vec_mulmod(ctx, n, da, db, dc)
+        torch.cuda.synchronize()
+        idx = np.arange(0, n, 997)
+        got = inputs.to_ints(gpu.to_host(dc[:, torch.from_numpy(idx).cuda()]))
+        assert got == oracle.vec_mulmod(inputs.sample_ints(a, idx), inputs.sample_ints(b, idx), q)
+        assert gpu.moma_ctx_sync_status(ctx) == 0
+    finally:
+        gpu.moma_ctx_destroy(ctx)

@@ -44,6 +44,18 @@ def test_primes_table_regenerates_from_oracle():
         assert oracle.gen_prime(w, 0) == table[(w, 0)].q
 
 
+def test_package_prime_table_is_the_oracle_scripts_output():
+    """The library's table (paper_2501_07535_gb300/primes.json) is exactly what the oracle-only
+    script writes: every entry, both tables."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_primes", os.path.join(os.path.dirname(__file__), "golden",
+                                                                             "make_primes.py"))
+    mp = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mp)
+    assert mp.TABLE == inputs.PRIMES_JSON
+    assert mp.main(["--check"]) == 0
+
+
 def test_miller_rabin_matches_sympy():
     rng = random.Random(7)
     for _ in range(300):

@@ -171,3 +171,29 @@ def test_latency_grows_with_offered_load(monkeypatch):
     assert lo["p99_ms"] < 2.5 and lo["mean_ms"] < 1.5
     assert hi["mean_ms"] > 20 * lo["mean_ms"] and hi["p99_ms"] > 20 * lo["p99_ms"]
     assert 0.9 * capacity < hi["jobs_per_s"] < 1.05 * capacity
+
+
+def test_resident_memory_is_charged_to_the_budget():
+    """Tables and operand masters the executor keeps resident count against the budget: beside 250
+    resident bytes only two 100-byte jobs fit a 450-byte budget at a time, so the rest wait for
+    batches to complete (deferred), and a job that would fit the budget alone but not beside the
+    resident memory is refused."""
+
+    class ResidentExecutor(FakeExecutor):
+        def resident_bytes(self):
+            return 250
+
+    for policy in ("fifo", "class"):
+        jobs = _jobs(12, size=100)
+        ex = ResidentExecutor()
+        st = serve.Scheduler(ex, budget_bytes=450, slots=4, max_batch_jobs=64, policy=policy).run([0.0] * 12, jobs)
+        assert st.completed == 12 and st.rejected == 0, policy
+        assert all(len(seeds) <= 2 for _, _, seeds in ex.launches), policy
+        assert st.resident_bytes == 250 and st.max_inflight_bytes <= 200, policy
+        assert st.resident_bytes + st.max_inflight_bytes <= 450
+        assert st.deferred_for_memory > 0, policy
+        summ = st.summary()
+        assert summ["max_total_gb"] <= 450 / 1e9 + 1e-12
+        big = [inputs.Job(op="mul", width=256, n=300, seed=50)]
+        st2 = serve.Scheduler(ResidentExecutor(), budget_bytes=450, slots=4, policy=policy).run([0.0], big)
+        assert st2.rejected == 1 and st2.completed == 0, policy
