@@ -390,7 +390,7 @@ def headline(r):
                   "served_p99_ms_median": s["p99_ms_median"], "served_p99_ms_max": s["p99_ms_max"],
                   "served_p99_ms_runs": s["open_loop"]["p99_ms_runs"]})
     if r.get("c1_single_ntt"):
-        h["c1_latency_us"] = r["c1_single_ntt"]["us_per_call"]
+        h["c1_latency_us"] = min(r["c1_single_ntt"]["us_per_call"], r["c1_single_ntt"]["tuned_us_per_call"])
     if r.get("cpu_baseline"):
         h["cpu_oracle_ntt_per_s"] = r["cpu_baseline"]["value"]
     return h
@@ -456,7 +456,8 @@ def measure_e2e(ctx, xs, n, steps, warmup, barrier, chunks=None, nstreams=None):
 
 def run_profile(args):
     """Small cases for ncu captures (each op: one untimed call first, then `steps` calls):
-    ntt: batched forward 256-bit 2^20 NTTs; mul / add / axpy: the 2^24-element 256-bit vector op;
+    ntt: batched forward 2^20-point NTTs (--ntt-batch transforms, --profile-bits wide);
+    mul / add / sub / axpy: the vector op on 2^--profile-logn elements at --profile-bits;
     ntt768: 768-bit 2^16 NTTs (batch 8); mont_ntt / mont_mul: the 256-bit NTT and mulmod over a
     full-width modulus (its context's default schedule: Montgomery twiddles, word-based Barrett
     mulmod); mont_mul_redc: the same mulmod as two Montgomery products (engine 4); batch: the uneven batch at reduced sizes (2^10..2^16, 64 jobs); batch_large:
@@ -483,27 +484,31 @@ def run_profile(args):
         return
     full = op.startswith("mont_")
     redc = op == "mont_mul_redc"
-    width = 768 if op == "ntt768" else WIDTH
+    width = 768 if op == "ntt768" else args.profile_bits
     p = inputs.prime_full(width) if full else inputs.prime(width)
     q, Lw = p.q, p.L
     ctx = (moma.moma_ctx_create_full if full else moma.moma_ctx_create)(q, width)
-    if op in ("mul", "add", "axpy", "mont_mul", "mont_mul_redc"):
+    if op in ("mul", "add", "sub", "axpy", "mont_mul", "mont_mul_redc"):
+        vn = 1 << args.profile_logn
         if redc:
-            moma.moma_ctx_set_config(ctx, "mul", VEC_N, engine=4)
-        a = moma.to_device(inputs.residues(q, Lw, VEC_N, seed=1))
-        b = moma.to_device(inputs.residues(q, Lw, VEC_N, seed=2))
+            moma.moma_ctx_set_config(ctx, "mul", vn, engine=4)
+        a = moma.to_device(inputs.residues(q, Lw, vn, seed=1))
+        b = moma.to_device(inputs.residues(q, Lw, vn, seed=2))
         c = torch.empty_like(a)
         alpha = inputs.scalar_residue(q, 3)
         for _ in range(1 + args.steps):
             if op == "add":
-                moma.moma_vec_addmod(ctx, VEC_N, a, b, c)
+                moma.moma_vec_addmod(ctx, vn, a, b, c)
+            elif op == "sub":
+                moma.moma_vec_submod(ctx, vn, a, b, c)
             elif op == "axpy":
-                moma.moma_vec_axpymod(ctx, VEC_N, alpha, a, b, c)
+                moma.moma_vec_axpymod(ctx, vn, alpha, a, b, c)
             else:
-                moma.moma_vec_mulmod(ctx, VEC_N, a, b, c)
+                moma.moma_vec_mulmod(ctx, vn, a, b, c)
         torch.cuda.synchronize()
+        cfg = moma.moma_ctx_get_config(ctx, "mul" if op.endswith("mul") or redc else op, vn)
         moma.moma_ctx_destroy(ctx)
-        print(json.dumps({"profile": op, "n": VEC_N, "calls": 1 + args.steps}))
+        print(json.dumps({"profile": op, "bits": width, "n": vn, "calls": 1 + args.steps, "schedule": cfg}))
         return
     n = 1 << (16 if op == "ntt768" else LOGN)
     xs = np.stack([inputs.residues(q, Lw, n, seed=10 + t) for t in range(args.ntt_batch)])
@@ -512,8 +517,10 @@ def run_profile(args):
     for _ in range(1 + args.steps):
         moma.moma_ntt_fwd_many(ctx, n, args.ntt_batch, dx, dy)
     torch.cuda.synchronize()
+    cfg = moma.moma_ctx_get_config(ctx, "ntt_fwd", n)
     moma.moma_ctx_destroy(ctx)
-    print(json.dumps({"profile": op, "n": n, "batch": args.ntt_batch, "calls": 1 + args.steps}))
+    print(json.dumps({"profile": op, "bits": width, "n": n, "batch": args.ntt_batch, "calls": 1 + args.steps,
+                      "passes_per_call": _pass_count(cfg, n.bit_length() - 1), "schedule": cfg}))
     return
 
 
@@ -636,8 +643,9 @@ def run_c3_sweep(prod_peak, steps=2):
 
 def run_c1_latency(calls=200):
     """The single small transform: one forward cyclic NTT of 2^12 points at 256 bits, issued as
-    `calls` back-to-back calls on one stream; microseconds per call (launch and kernel), and the
-    same calls captured once in a CUDA graph and replayed."""
+    `calls` back-to-back calls on one stream; microseconds per call (launch and kernel) with the
+    default schedule, the same calls captured once in a CUDA graph and replayed, and the calls with
+    the schedule the autotuner picks for one transform of this size."""
     import torch
 
     from paper_2501_07535_gb300 import inputs, moma
@@ -658,11 +666,17 @@ def run_c1_latency(calls=200):
             gms = _timer(max(1, calls // 20))(g.replay, warm=2)
         except RuntimeError:
             gms = None
+        default_cfg = moma.moma_ctx_get_config(ctx, "ntt_fwd", n)
+        tuned_cfg, _ = moma.moma_autotune(ctx, "ntt_fwd", n, 1, st)  # the autotuner's pick for one transform
+        tms = _timer(calls)(f, warm=5)
     st.synchronize()
     assert moma.moma_ctx_sync_status(ctx) == 0
     moma.moma_ctx_destroy(ctx)
+    keys = ("engine", "tile_log", "max_logr", "cta_threads", "tight_regs")
     return {"n": n, "bits": 256, "calls": calls, "us_per_call": round(ms * 1e3, 2),
-            "graph_us_per_call": round(gms * 1e3 / 20, 2) if gms is not None else None}
+            "graph_us_per_call": round(gms * 1e3 / 20, 2) if gms is not None else None,
+            "schedule": [default_cfg[k] for k in keys], "tuned_us_per_call": round(tms * 1e3, 2),
+            "tuned_schedule": [tuned_cfg[k] for k in keys]}
 
 
 def run_uneven_batch(steps, warmup, n_jobs=256, seed=0):
@@ -896,8 +910,10 @@ def main():
     ap.add_argument("--profile", action="store_true", help="small NTT-only case for ncu captures")
     ap.add_argument("--ntt-batch", type=int, default=8)
     ap.add_argument("--profile-op", default="ntt",
-                    choices=["ntt", "mul", "add", "axpy", "ntt768", "mont_ntt", "mont_mul", "mont_mul_redc", "batch",
-                             "batch_large"])
+                    choices=["ntt", "mul", "add", "sub", "axpy", "ntt768", "mont_ntt", "mont_mul", "mont_mul_redc",
+                             "batch", "batch_large"])
+    ap.add_argument("--profile-bits", type=int, default=WIDTH, help="container width of the profiled op")
+    ap.add_argument("--profile-logn", type=int, default=24, help="log2 elements of the profiled vector op")
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     ap.add_argument("--quick", action="store_true", help="skip the BLAS table and the transform sweep")
     args = ap.parse_args()

@@ -357,7 +357,8 @@ typedef enum {
                             final correction fired (Barrett contexts; a, b canonical)            */
   MOMA_WORD_FIXED = 5,   /* out = a * w - s * q with w = b's element 0 and s the quotient estimate
                             from w's companion, before any correction: in [0, 3q) (Barrett
-                            contexts; w canonical; a any L-word value)                           */
+                            contexts; w canonical; a any L-word value; engine 1 or 2 as for
+                            the transforms' twiddle products)                                    */
   MOMA_WORD_MONT = 6,    /* out = a * b * R^-1 mod q, R = 2^W (full-width contexts; a, b < q)     */
   MOMA_WORD_BARRETT_FULL = 7 /* planes 0..L: r = a*b - s*q before the final subtractions, L+1 words,
                             in [0, 4q) (s the truncated quotient estimate from floor(2^(2W)/q));

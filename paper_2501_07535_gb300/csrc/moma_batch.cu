@@ -78,7 +78,7 @@ __device__ __forceinline__ void vec_tile(const VecJobArgs<L>& p, uint32_t tile) 
       case VEC_MUL: mulmod_barrett<L, false>(z, x, y, p.k); break;
       default: {
         uint32_t ax[L];
-        mulmod_fixed<L, false>(ax, x, p.alpha, p.alphap, p.k);
+        mulmod_fixed<L, 1>(ax, x, p.alpha, p.alphap, p.k);
         addmod<L>(z, ax, y, p.k.q);
       }
     }
@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks)
       const uint32_t local = t - sg.first;
       if (sg.kind == SEG_NTT) {
         switch (sg.L) {
-          case 4: ntt_tile<4, true>(*static_cast<const NttPassArgs<4>*>(sg.args), local, sm); break;
-          case 8: ntt_tile<8, true>(*static_cast<const NttPassArgs<8>*>(sg.args), local, sm); break;
-          case 12: ntt_tile<12, false>(*static_cast<const NttPassArgs<12>*>(sg.args), local, sm); break;
+          case 4: ntt_tile<4, 2>(*static_cast<const NttPassArgs<4>*>(sg.args), local, sm); break;
+          case 8: ntt_tile<8, 2>(*static_cast<const NttPassArgs<8>*>(sg.args), local, sm); break;
+          case 12: ntt_tile<12, 1>(*static_cast<const NttPassArgs<12>*>(sg.args), local, sm); break;
         }
       } else {
         switch (sg.L) {

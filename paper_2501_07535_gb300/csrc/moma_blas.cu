@@ -33,11 +33,12 @@ moma_config vec_config(const moma_ctx* ctx, int vec_op) {
   // (1.00x at 256 bits up to 1.2x at 768 bits; 0.9x at 1024 bits, where carry chains are kept);
   // carry chains for the other ops
   if (c.engine == 0) c.engine = (vec_op == VEC_MUL && ctx->L <= 24) ? 3 : 1;
-  // measured on GB300 at 2^24 elements: multiplications prefer one element per thread from
-  // 256 bits up, additions and axpy two; narrow widths take the widest vectors
+  // measured on GB300 at 2^24 elements: two elements per thread at 256 bits (the two products
+  // interleave: 430 against 453 us for mulmod), one for mulmod from 384 bits up, two for additions
+  // and axpy; narrow widths take the widest vectors
   if (c.vec_width == 0) {
     const int vm = vec_max_width(ctx->L);
-    const int pref = ctx->L <= 4 ? 4 : (vec_op == VEC_MUL ? 1 : 2);
+    const int pref = ctx->L <= 4 ? 4 : ((vec_op == VEC_MUL && ctx->L > 8) ? 1 : 2);
     c.vec_width = pref < vm ? pref : vm;
   }
   // tile_log: 0 = direct vector loads; 8..10 = operands staged by bulk copies in tiles of

@@ -82,7 +82,7 @@ __device__ __forceinline__ void vec_apply(uint32_t (&z)[L], const uint32_t (&x)[
     mulmod_barrett<L, ENG == 2, ENG == 3>(z, x, y, p.k);
   } else {
     uint32_t ax[L];
-    mulmod_fixed<L, ENG == 2>(ax, x, p.alpha, p.alphap, p.k);
+    mulmod_fixed<L, (ENG == 2 ? 2 : 1)>(ax, x, p.alpha, p.alphap, p.k);
     addmod<L>(z, ax, y, p.k.q);
   }
 }
@@ -117,10 +117,11 @@ __global__ void __launch_bounds__(256) vec_kernel(const __grid_constant__ VecArg
   }
 }
 
-template <int L, int OP, int V, int ENG, int FULL = 0>
-moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
-                           const uint32_t* alpha_host, cudaStream_t st) {
-  VecArgs<L> p;
+// Kernel arguments common to both forms (constants, axpy scalar); MOMA_ERR_INVALID_ARG for a
+// non-canonical scalar.
+template <int L, int OP, int FULL>
+moma_status fill_vec_args(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                          const uint32_t* alpha_host, VecArgs<L>& p) {
   p.a = a;
   p.b = b;
   p.c = c;
@@ -140,6 +141,21 @@ moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* 
       companion(ctx, al, p.alphap);
     }
   }
+  p.status = ctx->d_status;
+  p.wait_ns = ctx->wait_ns;
+  p.log_tile = 0;
+  p.inject = 0;
+  return MOMA_OK;
+}
+
+template <int L, int OP, int V, int ENG, int FULL = 0>
+moma_status run_vec(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
+                           const uint32_t* alpha_host, cudaStream_t st) {
+  VecArgs<L> p;
+  moma_status rc = fill_vec_args<L, OP, FULL>(ctx, n, a, b, c, alpha_host, p);
+  if (rc) return rc;
+  // 256-thread CTAs (at 768 bits, where one such CTA fills an SM's registers, three CTAs of 128
+  // threads measured 9% slower), as many per SM as fit
   static std::atomic<int> occ_cached{-1};  // per-instantiation occupancy, computed once
   int occ = occ_cached.load(std::memory_order_relaxed);
   if (occ < 0) {
@@ -294,37 +310,6 @@ __global__ void __launch_bounds__(kVecStagedThreads) vec_staged_kernel(const __g
 #pragma unroll
     for (int l = 0; l < L; ++l) p.c[(uint64_t)l * p.n + e] = z[l];
   }
-}
-
-// Kernel arguments common to both forms (constants, axpy scalar); MOMA_ERR_INVALID_ARG for a
-// non-canonical scalar.
-template <int L, int OP, int FULL>
-moma_status fill_vec_args(moma_ctx* ctx, size_t n, const uint32_t* a, const uint32_t* b, uint32_t* c,
-                          const uint32_t* alpha_host, VecArgs<L>& p) {
-  p.a = a;
-  p.b = b;
-  p.c = c;
-  p.n = n;
-  fill_modk<L>(ctx, p.k);
-  for (int i = 0; i < L; ++i) {
-    p.alpha[i] = 0;
-    p.alphap[i] = 0;
-  }
-  if (OP == VEC_AXPY) {
-    BigU al = BigU::from_words(alpha_host, L);
-    if (cmp(al, ctx->Q) >= 0) return MOMA_ERR_INVALID_ARG;
-    if (FULL != 0) {  // alpha R mod q: one Montgomery product gives alpha * x
-      ctx->red->mulmod(al, BigU::from_words(ctx->k.R0, L)).to_words(p.alpha, L);
-    } else {
-      al.to_words(p.alpha, L);
-      companion(ctx, al, p.alphap);
-    }
-  }
-  p.status = ctx->d_status;
-  p.wait_ns = ctx->wait_ns;
-  p.log_tile = 0;
-  p.inject = 0;
-  return MOMA_OK;
 }
 
 template <int L, int OP, int ENG, int FULL = 0>

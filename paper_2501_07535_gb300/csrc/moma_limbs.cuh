@@ -465,31 +465,30 @@ MOMA_DEV void mulmod_barrett(uint32_t (&c)[L], const uint32_t (&a)[L], const uin
 //   s = floor(a*wp / 2^(32L)) (truncated, exact or one less);  r = a*w - s*q mod 2^(32L).
 // For any a < 2^(32L): a*w/q - s < 3, so r lies in [0, 3q), which fits the container.
 // Used for twiddle factors (tables carry the companion) and for the axpy scalar.
-// WIDE: the truncated high half a*wp by whole mad.wide products, the two low halves by carry
-// chains (on GB300 2-3% faster than either form throughout: it splits the work between the
-// multiply pipe and the integer ALU pipe).
-template <int L, bool WIDE = false>
+// FE picks the word-product form, splitting the work between the multiply pipe (a whole product
+// by mad.wide: 4 cycles; a lo/hi carry-chain pair: 6) and the integer ALU pipe (the carry
+// handling of a whole product costs more ALU instructions than that of a carry chain):
+//   1: carry chains throughout;
+//   2: whole products for the truncated high half a*wp, carry chains for the low halves a*w and
+//      s*nq (on GB300 2-3% faster than either uniform form at 256 and 384 bits; the reverse split,
+//      carry chains for the high half and whole products for the low halves, measured 4-21% slower).
+template <int L, int FE = 1>
 MOMA_DEV void mulmod_fixed_lazy(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
                                 const uint32_t (&wp)[L], const ModK<L>& k) {
   uint32_t s[L];
 #pragma unroll
   for (int i = 0; i < L; ++i) r[i] = 0u;
-  if constexpr (WIDE) {
-    mul_hi_trunc_w<L>(s, a, wp);
-    mul_lo_acc<L>(r, a, w);
-    mul_lo_acc<L>(r, s, k.nq);
-  } else {
-    mul_hi_trunc<L>(s, a, wp);
-    mul_lo_acc<L>(r, a, w);
-    mul_lo_acc<L>(r, s, k.nq);
-  }
+  if constexpr (FE == 2) mul_hi_trunc_w<L>(s, a, wp);
+  else mul_hi_trunc<L>(s, a, wp);
+  mul_lo_acc<L>(r, a, w);
+  mul_lo_acc<L>(r, s, k.nq);
 }
 
 // Canonical form: r in [0, 3q) -> [0, q).
-template <int L, bool WIDE = false>
+template <int L, int FE = 1>
 MOMA_DEV void mulmod_fixed(uint32_t (&r)[L], const uint32_t (&a)[L], const uint32_t (&w)[L],
                            const uint32_t (&wp)[L], const ModK<L>& k) {
-  mulmod_fixed_lazy<L, WIDE>(r, a, w, wp, k);
+  mulmod_fixed_lazy<L, FE>(r, a, w, wp, k);
   cond_sub<L>(r, k.q2);  // [0,3q) -> [0,2q)
   cond_sub<L>(r, k.q);   // -> [0,q)
 }

@@ -16,12 +16,13 @@ constexpr int kNttMaxThreads = 256;  // per CTA; the launch may use 32, 64, 128 
 // measured 2-4% faster than 128); from 512 bits up the full 255.  TIGHT variants (at most 128
 // threads per CTA) are compiled for 64 registers up to 256 bits, 102 at 384 bits and 170 at 768
 // bits, without spills, for more resident CTAs.
-template <int L, bool WIDE, bool TIGHT>
+// FE: the product form of the twiddle multiplications (mulmod_fixed_lazy; the schedule's engine).
+template <int L, int FE, bool TIGHT>
 __global__ void __launch_bounds__(TIGHT ? 128 : kNttMaxThreads,
                                   TIGHT ? (L <= 8 ? 8 : (L == 12 ? 5 : 3)) : (L <= 12 ? 3 : 1))
     ntt_pass_kernel(const __grid_constant__ NttPassArgs<L> p) {
   extern __shared__ __align__(16) uint32_t sm[];
-  ntt_tile<L, WIDE>(p, blockIdx.x, sm);
+  ntt_tile<L, FE>(p, blockIdx.x, sm);
 }
 
 // Full-width contexts: the same pass with Montgomery arithmetic (carry chains, canonical values).
@@ -121,7 +122,7 @@ moma_status gen_table(const moma_ctx* ctx, uint32_t* dst, uint64_t count, uint64
   return cuda_status(cudaGetLastError());
 }
 
-template <int L, bool WIDE, bool TIGHT>
+template <int L, int FE, bool TIGHT>
 moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
                             const uint32_t* src2, uint32_t* dst, uint32_t flags, int threads, cudaStream_t st) {
   NttPassArgs<L> a;
@@ -130,7 +131,7 @@ moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t co
   static std::atomic<uint64_t> attr_done{0};  // one bit per device: the attribute is per device
   const uint64_t dev_bit = 1ull << (ctx->device & 63);
   if (!(attr_done.load(std::memory_order_acquire) & dev_bit)) {
-    if (cudaFuncSetAttribute(ntt_pass_kernel<L, WIDE, TIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(ntt_pass_kernel<L, FE, TIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              L * 4 << max_tile_log(L)) != cudaSuccess)
       return MOMA_ERR_CUDA;
     attr_done.fetch_or(dev_bit, std::memory_order_release);
@@ -138,7 +139,7 @@ moma_status run_pass(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t co
   const uint64_t grid = (uint64_t)count * a.tiles_per_transform;
   if (grid == 0) return MOMA_OK;
   if (grid > 0x7fffffffull) return MOMA_ERR_SIZE;
-  ntt_pass_kernel<L, WIDE, TIGHT><<<(unsigned)grid, threads, smem, st>>>(a);
+  ntt_pass_kernel<L, FE, TIGHT><<<(unsigned)grid, threads, smem, st>>>(a);
   return cuda_status(cudaGetLastError());
 }
 
@@ -164,28 +165,29 @@ moma_status run_pass_mont(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size
 }
 
 // One pass with the kernel the schedule picks: Montgomery for full-width contexts; otherwise the
-// product engine (carry chains or whole products) and the register cap.  From 512 bits up the
-// whole-product rows and the capped variant are not instantiated except at 768 bits (they need
-// more registers than a thread has), so the engine and cap settings fall back to carry chains.
+// product form of the twiddle multiplications (engine 1 or 2: mulmod_fixed_lazy's FE) and the
+// register cap.  From 512 bits up only carry chains are instantiated, except at 768 bits (engine 2
+// and the capped variant); other settings fall back to carry chains.
 template <int L>
 moma_status run_pass_for(moma_ctx* ctx, const Plan* pl, const PassDesc& d, size_t count, const uint32_t* src,
                          const uint32_t* src2, uint32_t* dst, uint32_t flags, const moma_config& cfg,
                          cudaStream_t st) {
   if (ctx->mont) return run_pass_mont<L>(ctx, pl, d, count, src, src2, dst, flags, cfg.cta_threads, st);
-  const bool wide = cfg.engine == 2;
+  const int fe = cfg.engine;
   const int th = cfg.cta_threads;
   const bool tight = cfg.tight_regs != 0 && th <= 128;
   if constexpr (L <= 12) {
-    return wide ? (tight ? run_pass<L, true, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                         : run_pass<L, true, false>(ctx, pl, d, count, src, src2, dst, flags, th, st))
-                : (tight ? run_pass<L, false, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                         : run_pass<L, false, false>(ctx, pl, d, count, src, src2, dst, flags, th, st));
+    if (fe == 2)
+      return tight ? run_pass<L, 2, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                   : run_pass<L, 2, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    return tight ? run_pass<L, 1, true>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                 : run_pass<L, 1, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   } else if constexpr (L == 24) {
-    if (tight) return run_pass<L, false, true>(ctx, pl, d, count, src, src2, dst, flags, th, st);
-    return wide ? run_pass<L, true, false>(ctx, pl, d, count, src, src2, dst, flags, th, st)
-                : run_pass<L, false, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    if (tight) return run_pass<L, 1, true>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    return fe == 2 ? run_pass<L, 2, false>(ctx, pl, d, count, src, src2, dst, flags, th, st)
+                   : run_pass<L, 1, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   } else {
-    return run_pass<L, false, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
+    return run_pass<L, 1, false>(ctx, pl, d, count, src, src2, dst, flags, th, st);
   }
 }
 

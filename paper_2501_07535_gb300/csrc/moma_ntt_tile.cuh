@@ -109,8 +109,8 @@ struct NttPassArgs {
 enum { F_PRETW = 1, F_SCALE = 2, F_POINTWISE = 4, F_LAST = 8, F_PSI_IN = 16, F_PSI_OUT = 32 };
 
 // DIF butterfly on lazy values: a, b in [0, 4q) -> (a + b, (a - b) * w) both in [0, 4q).
-// With MUL false the twiddle is 1.
-template <int L, bool WIDE>
+// With MUL false the twiddle is 1.  FE: the product form of mulmod_fixed_lazy.
+template <int L, int FE>
 __device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&b)[L], bool mul,
                                                    const uint32_t* table, uint32_t entry, const ModK<L>& k) {
   uint32_t x[L], d[L];
@@ -121,7 +121,7 @@ __device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&
   if (mul) {
     uint32_t w[L], wp[L];
     twiddle_load<L>(table, entry, w, wp);
-    mulmod_fixed_lazy<L, WIDE>(b, d, w, wp, k);  // [0, 3q)
+    mulmod_fixed_lazy<L, FE>(b, d, w, wp, k);  // [0, 3q)
   } else {
     cond_sub<L>(d, k.q4);
 #pragma unroll
@@ -133,25 +133,25 @@ __device__ __forceinline__ void dif_butterfly_lazy(uint32_t (&a)[L], uint32_t (&
 
 // The modular arithmetic of a transform pass, by reduction.
 // Barrett contexts (B = W - 4): lazy values in [0, 4q) inside a transform, twiddles with Barrett
-// companions (mulmod_fixed_lazy), canonical store at the end.
-template <int L, bool WIDE>
+// companions (mulmod_fixed_lazy with product form FE), canonical store at the end.
+template <int L, int FE>
 struct BarrettArith {
   static __device__ __forceinline__ void pointwise(uint32_t (&v)[L], const uint32_t (&u)[L], const ModK<L>& k) {
     uint32_t t[L];
-    mulmod_barrett<L, WIDE>(t, v, u, k);
+    mulmod_barrett<L, FE == 2>(t, v, u, k);
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = t[l];
   }
   static __device__ __forceinline__ void mul_fixed(uint32_t (&v)[L], const uint32_t (&w)[L], const uint32_t (&wp)[L],
                                                    const ModK<L>& k) {
     uint32_t t[L];
-    mulmod_fixed_lazy<L, WIDE>(t, v, w, wp, k);
+    mulmod_fixed_lazy<L, FE>(t, v, w, wp, k);
 #pragma unroll
     for (int l = 0; l < L; ++l) v[l] = t[l];
   }
   static __device__ __forceinline__ void butterfly(uint32_t (&a)[L], uint32_t (&b)[L], bool mul, const uint32_t* table,
                                                    uint32_t entry, const ModK<L>& k) {
-    dif_butterfly_lazy<L, WIDE>(a, b, mul, table, entry, k);
+    dif_butterfly_lazy<L, FE>(a, b, mul, table, entry, k);
   }
   static __device__ __forceinline__ void finish(uint32_t (&v)[L], const ModK<L>& k) {  // [0, 4q) -> [0, q)
     cond_sub<L>(v, k.q2);
@@ -301,9 +301,9 @@ __device__ __forceinline__ void ntt_tile_impl(const NttPassArgs<L>& p, uint32_t 
   }
 }
 
-template <int L, bool WIDE>
+template <int L, int FE>
 __device__ __forceinline__ void ntt_tile(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm) {
-  ntt_tile_impl<L, BarrettArith<L, WIDE>>(p, tile, sm);
+  ntt_tile_impl<L, BarrettArith<L, FE>>(p, tile, sm);
 }
 
 // Host: fill the arguments of one pass (count transforms of length 2^logn).

@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(256) word_kernel(const __grid_constant__ WordA
     }
     case MOMA_WORD_FIXED: {
       uint32_t r[L];
-      if (p.engine == 2) mulmod_fixed_lazy<L, true>(r, a, p.w, p.wp, p.k);
-      else mulmod_fixed_lazy<L, false>(r, a, p.w, p.wp, p.k);
+      if (p.engine == 2) mulmod_fixed_lazy<L, 2>(r, a, p.w, p.wp, p.k);
+      else mulmod_fixed_lazy<L, 1>(r, a, p.w, p.wp, p.k);
 #pragma unroll
       for (int l = 0; l < L; ++l) o[l] = r[l];
       break;

@@ -135,6 +135,10 @@ def test_config_rejects_invalid(gpu):
             gpu.moma_ctx_set_config(ctx, "ntt_fwd", 1 << 10, engine=7)
         with pytest.raises(gpu.MomaError):
             gpu.moma_ctx_set_config(ctx, "mul", 1 << 10, vec_width=3)
+        with pytest.raises(gpu.MomaError):  # the staged tile is fixed per width (2^9 at 256 bits)
+            gpu.moma_ctx_set_config(ctx, "mul", 1 << 10, tile_log=8)
+        with pytest.raises(gpu.MomaError):
+            gpu.moma_ctx_set_config(ctx, "ntt_fwd", 1 << 10, engine=3)
         with pytest.raises(gpu.MomaError):
             gpu.moma_ctx_set_config(ctx, 99, 1 << 10)
         with pytest.raises(gpu.MomaError):
