@@ -492,6 +492,9 @@ def run_profile(args):
         vn = 1 << args.profile_logn
         if redc:
             moma.moma_ctx_set_config(ctx, "mul", vn, engine=4)
+        elif args.profile_tile:  # operands staged in shared memory by bulk copies
+            cur = moma.moma_ctx_get_config(ctx, op, vn)
+            moma.moma_ctx_set_config(ctx, op, vn, engine=cur["engine"], tile_log=args.profile_tile)
         a = moma.to_device(inputs.residues(q, Lw, vn, seed=1))
         b = moma.to_device(inputs.residues(q, Lw, vn, seed=2))
         c = torch.empty_like(a)
@@ -914,6 +917,7 @@ def main():
                              "batch", "batch_large"])
     ap.add_argument("--profile-bits", type=int, default=WIDTH, help="container width of the profiled op")
     ap.add_argument("--profile-logn", type=int, default=24, help="log2 elements of the profiled vector op")
+    ap.add_argument("--profile-tile", type=int, default=0, help="staged tile (log2) of the profiled vector op (0: direct)")
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     ap.add_argument("--quick", action="store_true", help="skip the BLAS table and the transform sweep")
     args = ap.parse_args()

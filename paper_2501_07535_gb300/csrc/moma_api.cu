@@ -246,7 +246,8 @@ static moma_status nega_ntt_call(moma_ctx* ctx, size_t n, size_t count, bool inv
   if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
   if (count > ((size_t)1 << 20)) return MOMA_ERR_SIZE;
   return launch_ntt_cfg(ctx, lg, count, inverse, in, out,
-                        ntt_config(ctx, inverse ? MOMA_OP_NTT_INV : MOMA_OP_NTT_FWD, lg), (cudaStream_t)stream, true);
+                        ntt_config(ctx, inverse ? MOMA_OP_NTT_INV : MOMA_OP_NTT_FWD, lg, count), (cudaStream_t)stream,
+                        true);
 }
 
 moma_status moma_ntt_fwd_negacyclic(moma_ctx* ctx, size_t n, size_t count, const uint32_t* in, uint32_t* out,
@@ -265,7 +266,7 @@ moma_status moma_polymul_negacyclic(moma_ctx* ctx, size_t n, const uint32_t* a, 
   if (!aligned4(a) || !aligned4(b) || !aligned4(c)) return MOMA_ERR_ALIGN;
   int lg = log2_exact(n);
   if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-  return launch_polymul_cfg(ctx, lg, a, b, c, ntt_config(ctx, MOMA_OP_POLYMUL, lg), (cudaStream_t)stream, true);
+  return launch_polymul_cfg(ctx, lg, a, b, c, ntt_config(ctx, MOMA_OP_POLYMUL, lg, 1), (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

@@ -99,7 +99,9 @@ moma_status launch_vec_wide(moma_ctx* ctx, int op, size_t n, const uint32_t* a, 
 // moma_ntt.cu
 int default_tile_log(int L);
 int max_tile_log(int L);                 // shared-memory limit
-moma_config ntt_config(const moma_ctx* ctx, int op, int logn);  // effective (defaults filled)
+// Effective schedule (defaults filled) for `count` transforms of 2^logn points in one call; count 0:
+// the default for large batches (persistent batch tiles).
+moma_config ntt_config(const moma_ctx* ctx, int op, int logn, size_t count = 0);
 bool ntt_config_valid(int L, int logn, const moma_config& c);
 moma_status ntt_prepare(moma_ctx* ctx);  // primality, generator (takes ctx->lock)
 moma_status get_plan(moma_ctx* ctx, int logn, bool inverse, int tile_log, int max_logr, Plan** out,

@@ -61,7 +61,7 @@ extern "C" moma_status moma_ntt_fwd_noalloc(moma_ctx* ctx, size_t n, const uint3
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return MOMA_ERR_CUDA;
   if (dev != ctx->device) return MOMA_ERR_INVALID_ARG;
-  const moma_config cfg = ntt_config(ctx, MOMA_OP_NTT_FWD, lg);
+  const moma_config cfg = ntt_config(ctx, MOMA_OP_NTT_FWD, lg, 1);  // the schedule moma_ntt_fwd uses
   Plan* pl = find_plan(ctx, lg, false, cfg.tile_log, cfg.max_logr);
   if (!pl) return MOMA_ERR_INVALID_ARG;  // twiddle tables not built yet: call moma_ntt_fwd once
   uint32_t* scratch = noalloc_scratch(dev);  // resolved when the context was created

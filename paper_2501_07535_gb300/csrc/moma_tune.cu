@@ -49,7 +49,7 @@ extern "C" moma_status moma_ctx_get_config(moma_ctx* ctx, int op, size_t n, moma
   if (is_ntt_op(op)) {
     const int lg = log2_of(n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-    *cfg = ntt_config(ctx, op, lg);  // takes the context's lock for the lookup
+    *cfg = ntt_config(ctx, op, lg, 1);  // a single transform's; takes the context's lock for the lookup
     return MOMA_OK;
   }
   if (is_vec_op(op)) {
@@ -171,7 +171,7 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   rc = moma_ctx_set_config(ctx, op, n, &best_c);
   if (rc) return rc;
   if (best)  // the effective schedule, defaults filled in (as moma_ctx_get_config reports it)
-    *best = lg >= 0 ? ntt_config(ctx, op, lg) : vec_config(ctx, op - MOMA_OP_ADD);
+    *best = lg >= 0 ? ntt_config(ctx, op, lg, 1) : vec_config(ctx, op - MOMA_OP_ADD);
   if (best_us) *best_us = best_t;
   return MOMA_OK;
 }

@@ -259,3 +259,26 @@ def test_ntt_argument_errors(gpu, ctxs):
     finally:
         torch.cuda.synchronize()
         lib.moma_ctx_destroy(hp)
+
+
+@pytest.mark.parametrize("width", [128, 256, 384])
+def test_ntt_small_and_large_work_defaults(gpu, ctxs, width):
+    """Without a schedule set, a call of count transforms of n points takes the default for little
+    work when count * n <= 2^19 (2^9 tiles) and the batch default above (2^10 tiles).  The same
+    transforms through both: every output equals the oracle's (first transform) and the two calls'
+    outputs are identical."""
+    p = inputs.prime(width)
+    n = 1 << 16
+    xs = np.stack([inputs.residues(p.q, p.L, n, seed=90 + t) for t in range(16)])
+    dx = gpu.to_device(xs)
+    small, large = torch.empty_like(dx), torch.empty_like(dx)
+    gpu.moma_ntt_fwd_many(ctxs[width], n, 8, dx[:8], small[:8])   # 2^19 points: little work
+    gpu.moma_ntt_fwd_many(ctxs[width], n, 16, dx, large)          # 2^20 points: batch default
+    gpu.moma_ntt_fwd_many(ctxs[width], n, 8, dx[8:], small[8:])
+    torch.cuda.synchronize()
+    assert torch.equal(small, large)
+    assert inputs.to_ints(gpu.to_host(large[0])) == oracle.ntt_fwd(inputs.to_ints(xs[0]), p.q)
+    back = torch.empty_like(dx)
+    gpu.moma_ntt_inv_many(ctxs[width], n, 4, small[:4], back[:4])
+    torch.cuda.synchronize()
+    assert torch.equal(back[:4], dx[:4])
