@@ -341,7 +341,8 @@ moma_status moma_ctx_get_config(moma_ctx *ctx, int op, size_t n, moma_config *cf
  * the NTT ops) on scratch buffers of the context's device, with CUDA events on `stream`,
  * keep the fastest in the context (as if set by moma_ctx_set_config) and write it to
  * *best (may be NULL) and its time per call in microseconds to *best_us (may be NULL).
- * Synchronous.  Allocates and frees its scratch buffers. */
+ * Synchronous.  Allocates and frees its scratch buffers; transform plans (twiddle tables) that
+ * it builds for candidates other than the winner are freed before it returns. */
 moma_status moma_autotune(moma_ctx *ctx, int op, size_t n, size_t count, void *stream,
                           moma_config *best, double *best_us);
 

@@ -5,6 +5,8 @@
 // the largest radix of one Stockham pass, and the vector width of the BLAS kernels.  Every
 // schedule computes bit-identical results; only speed differs.  The autotuner times each
 // candidate with CUDA events on the caller's stream and keeps the fastest.
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "moma_internal.hpp"
@@ -89,11 +91,11 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
     if (count == 0) count = 1;
     if (op == MOMA_OP_POLYMUL) count = 1;
-    // CTA size and tile go together: 2^3..2^4 elements per thread; radices leave 8 to 32
-    // groups per tile.
+    // CTA size and tile go together: 2^2..2^4 elements per thread (2^2 for calls with little work,
+    // where more CTAs per call pay); radices leave 8 to 32 groups per tile.
     for (int engine = 1; engine <= 2; ++engine)
       for (int th = 32, lth = 5; th <= 256; th *= 2, ++lth)
-        for (int t = 0; t <= 1; ++t) {
+        for (int t = -1; t <= 1; ++t) {
           const int tl = lth + 3 + t;
           if (tl > max_tile_log(ctx->L)) continue;
           if (lg <= tl) {
@@ -139,6 +141,13 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
     }
   };
 
+  // plans that exist before tuning stay; those built only for losing candidates are freed after
+  std::set<std::tuple<int, int, int, int, int>> plans_before;
+  if (lg >= 0) {
+    std::lock_guard<std::mutex> g(ctx->lock);
+    for (const auto& kv : ctx->plans) plans_before.insert(kv.first);
+  }
+
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MOMA_ERR_CUDA;
   double best_t = 1e30;
@@ -167,6 +176,23 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (lg >= 0 && cudaStreamSynchronize(st) == cudaSuccess) {
+    // every candidate's transforms have finished: free the twiddle tables built only for candidates
+    // that lost (at 2^24 points and 384 bits each plan holds about 1.6 GB)
+    const int keep_t = best_c.tile_log, keep_r = lg <= best_c.tile_log ? 0 : best_c.max_logr;
+    std::lock_guard<std::mutex> g(ctx->lock);
+    for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+      const auto& key = it->first;
+      const bool kept = plans_before.count(key) || std::get<0>(key) != lg ||
+                        (rc == MOMA_OK && std::get<2>(key) == keep_t && std::get<3>(key) == keep_r);
+      if (kept) {
+        ++it;
+      } else {
+        free_plan(it->second);
+        it = ctx->plans.erase(it);
+      }
+    }
+  }
   if (rc) return rc;
   rc = moma_ctx_set_config(ctx, op, n, &best_c);
   if (rc) return rc;

@@ -173,3 +173,27 @@ def test_schedule_table_round_trip(gpu, tmp_path):
     finally:
         gpu.moma_ctx_destroy(ctx)
         gpu.moma_ctx_destroy(ctx2)
+
+
+def test_autotune_keeps_only_the_winners_plan(gpu):
+    """The autotuner builds a plan (twiddle tables) per candidate split; the losers' plans are freed,
+    so the context holds at most one more plan than before (the winner's), and the winner's schedule
+    still gives the oracle's transform."""
+    p = inputs.prime(256)
+    ctx = gpu.moma_ctx_create(p.q, 256)
+    try:
+        n = 1 << 14
+        x = inputs.residues(p.q, p.L, n, 31)
+        dx = gpu.to_device(x)
+        dy = torch.empty_like(dx)
+        gpu.moma_ntt_fwd(ctx, n, dx, dy)  # the default schedule's plan
+        torch.cuda.synchronize()
+        base = gpu.moma_ctx_device_bytes(ctx)
+        gpu.moma_autotune(ctx, "ntt_fwd", n, 1)
+        after = gpu.moma_ctx_device_bytes(ctx)
+        assert base <= after <= 2 * base
+        gpu.moma_ntt_fwd(ctx, n, dx, dy)
+        torch.cuda.synchronize()
+        assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
+    finally:
+        gpu.moma_ctx_destroy(ctx)
