@@ -91,11 +91,12 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
     if (count == 0) count = 1;
     if (op == MOMA_OP_POLYMUL) count = 1;
-    // CTA size and tile go together: 2^2..2^4 elements per thread (2^2 for calls with little work,
-    // where more CTAs per call pay); radices leave 8 to 32 groups per tile.
+    // CTA size and tile go together: 2^1..2^4 elements per thread (2^1 and 2^2 for calls with
+    // little work, where more CTAs and fewer butterflies per thread pay); radices leave 8 to 32
+    // groups per tile.
     for (int engine = 1; engine <= 2; ++engine)
       for (int th = 32, lth = 5; th <= 256; th *= 2, ++lth)
-        for (int t = -1; t <= 1; ++t) {
+        for (int t = -2; t <= 1; ++t) {
           const int tl = lth + 3 + t;
           if (tl > max_tile_log(ctx->L)) continue;
           if (lg <= tl) {

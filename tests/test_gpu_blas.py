@@ -251,6 +251,9 @@ def test_blas_staged_wait_runs_out(gpu):
     ctx = gpu.moma_ctx_create(q, 256)
     try:
         gpu.moma_ctx_set_config(ctx, "mul", n, engine=3, tile_log=9)
+        lib = gpu.lib()
+        assert lib.moma_ctx_set_wait_limit(ctx, 0) == 1 and lib.moma_ctx_set_wait_limit(None, 5) == 1
+        assert lib.moma_ctx_inject_missing_copy(None) == 1
         gpu.moma_ctx_set_wait_limit(ctx, 2_000_000)  # 2 ms
         a = inputs.residues(q, L, n, 21)
         b = inputs.residues(q, L, n, 22)
