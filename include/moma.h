@@ -101,7 +101,7 @@ int moma_ctx_limbs(const moma_ctx *ctx);
 
 /* Bytes of device memory the context holds right now: the twiddle tables of every
  * transform plan built so far (one per size, direction and schedule; about n entries of
- * 2L words per direction), the tables of their one-launch form where used, and its status word.  Scratch buffers of calls in flight are not
+ * 2L words per direction) and its status word.  Scratch buffers of calls in flight are not
  * included (they come from the stream-ordered pool and are released by the calls).  For
  * admission control by memory budget.  0 for NULL. */
 size_t moma_ctx_device_bytes(const moma_ctx *ctx);
@@ -315,11 +315,6 @@ typedef enum {
  *              contexts always take 1).
  *   cta_threads transforms: threads per CTA (32, 64, 128 or 256).  Each CTA owns one tile;
  *              small CTAs synchronise fewer warps between butterfly stages.
- *   dataflow   transforms: 1 = all passes of a call in one persistent launch, each tile waiting
- *              (bounded) only for the tiles of the previous pass that it reads, so that a pass
- *              starts while the previous one drains (Barrett contexts of 128 to 384 bits, plans of 2
- *              to 6 passes, output not an input; other calls take one launch per pass); 0 = one
- *              launch per pass.  Identical results either way.
  *   tight_regs transforms: 1 = kernels compiled for fewer registers per thread (64 up to 256
  *              bits, 102 at 384 bits, 170 at 768 bits) so that more CTAs of at most 128
  *              threads are resident; 0 = no cap beyond the default (85 up to 384 bits).  The
@@ -331,7 +326,6 @@ typedef struct {
   int vec_width;
   int cta_threads;
   int tight_regs;
-  int dataflow;
 } moma_config;
 
 /* Set / read the schedule used for `op` at size n (transforms: exact n; BLAS: every n).

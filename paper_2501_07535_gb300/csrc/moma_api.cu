@@ -127,7 +127,7 @@ size_t moma_ctx_device_bytes(const moma_ctx* ctx) {
   if (!ctx) return 0;
   std::lock_guard<std::mutex> g(ctx->lock);
   size_t b = sizeof(int);  // the status word
-  for (const auto& kv : ctx->plans) b += kv.second->table_bytes + kv.second->flow.bytes;
+  for (const auto& kv : ctx->plans) b += kv.second->table_bytes;
   return b;
 }
 

@@ -38,17 +38,6 @@ struct PassDesc {
   uint64_t tw_count = 0;
 };
 
-// Tables of the one-launch (dataflow) form of a plan, for one transform (moma_ntt_flow.cuh):
-// one device allocation holding the queue order of every pass, the producer count of every tile
-// and the consumer lists (CSR) of every tile, built on first use.
-struct FlowTables {
-  uint32_t* d = nullptr;
-  size_t bytes = 0;
-  uint32_t total = 0;  // tiles of all passes
-  uint32_t tiles[8] = {}, base[8] = {};
-  uint32_t *order = nullptr, *req = nullptr, *cons_off = nullptr, *cons_idx = nullptr;
-};
-
 struct Plan {
   int logn = 0;
   bool inverse = false;
@@ -60,7 +49,6 @@ struct Plan {
   size_t table_bytes = 0;         // its size
   uint32_t scale[kMaxL] = {}, scalep[kMaxL] = {};  // n^-1 and its companion (inverse)
   int tile_log = 0;                                // log2 of the CTA tile (elements)
-  mutable FlowTables flow;                         // built on first one-launch use (under the context's lock)
 };
 
 }  // namespace moma

@@ -27,7 +27,6 @@
 
 #include "moma_internal.hpp"
 #include "moma_limbs.cuh"
-#include "moma_ntt_flow.cuh"
 #include "moma_ntt_pass.cuh"
 #include "moma_ntt_tile.cuh"
 
@@ -108,7 +107,6 @@ bool ntt_config_valid(int L, int logn, const moma_config& c) {
       c.cta_threads != 256)
     return false;
   if (c.tight_regs != 0 && (c.tight_regs != 1 || c.cta_threads > 128)) return false;
-  if (c.dataflow != 0 && c.dataflow != 1) return false;
   return true;
 }
 
@@ -157,7 +155,6 @@ void companion(const moma_ctx* ctx, const BigU& w, uint32_t* out) {
 void free_plan(Plan* p) {
   if (!p) return;
   if (p->d_tables) cudaFree(p->d_tables);
-  if (p->flow.d) cudaFree(p->flow.d);
   delete p;
 }
 
@@ -294,17 +291,6 @@ static moma_status run_pass_l(moma_ctx* ctx, const Plan* pl, const PassDesc& d, 
   }
 }
 
-// Flags of pass i of P: canonical store in the last pass, the fused pointwise product and n^-1 in
-// the first; negacyclic plans apply psi at the first load (forward) or the last store (inverse).
-static uint32_t pass_flags(const Plan* pl, size_t i, size_t P, bool pointwise) {
-  uint32_t flags = (i + 1 == P) ? F_LAST : 0;
-  if (i == 0 && pointwise) flags |= F_POINTWISE;
-  if (i == 0 && pl->inverse && !pl->negacyclic) flags |= F_SCALE;  // negacyclic: n^-1 is in psi
-  if (i == 0 && pl->negacyclic && !pl->inverse) flags |= F_PSI_IN;
-  if (i + 1 == P && pl->negacyclic && pl->inverse) flags |= F_PSI_OUT;
-  return flags;
-}
-
 // Run every pass of a plan: in -> [s1 -> s2 -> s1 ...] -> out, with caller-provided
 // intermediate buffers (each count*L*n words; s1 unused for one pass, s2 for up to two).  The
 // first pass can fuse a pointwise product with in2 (polymul) and, for the inverse, the n^-1
@@ -316,211 +302,22 @@ moma_status run_plan_buffers(moma_ctx* ctx, const Plan* pl, size_t count, const 
   const uint32_t* src = in;
   for (size_t i = 0; i < P && rc == MOMA_OK; ++i) {
     uint32_t* dst = (i + 1 == P) ? out : ((i % 2 == 0) ? s1 : s2);
-    rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst,
-                    pass_flags(pl, i, P, in2 != nullptr), cfg, st);
+    uint32_t flags = (i + 1 == P) ? F_LAST : 0;
+    if (i == 0 && in2) flags |= F_POINTWISE;
+    if (i == 0 && pl->inverse && !pl->negacyclic) flags |= F_SCALE;  // negacyclic: n^-1 is in psi
+    if (i == 0 && pl->negacyclic && !pl->inverse) flags |= F_PSI_IN;
+    if (i + 1 == P && pl->negacyclic && pl->inverse) flags |= F_PSI_OUT;
+    rc = run_pass_l(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst, flags, cfg, st);
     src = dst;
   }
   return rc;
 }
 
-// ------------------------------------------------------------------ one-launch (dataflow) form
-
-// Calls the one-launch form covers: Barrett contexts of 128 to 384 bits, 2 to kFlowMaxPasses
-// passes, counters that fit 32-bit queue positions, and an output that is not an input: tiles of
-// the last pass run while tiles of the first may still read the input (in place, the per-pass
-// launches are used).
-static bool flow_eligible(const moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
-                          const uint32_t* out) {
-  if (ctx->mont || (ctx->L != 4 && ctx->L != 8 && ctx->L != 12)) return false;
-  if (out == in || out == in2) return false;
-  const size_t P = pl->passes.size();
-  if (P < 2 || P > (size_t)kFlowMaxPasses) return false;
-  uint64_t total = 0;
-  for (const auto& d : pl->passes) total += (1ull << pl->logn) >> (d.logR + d.logG);
-  return (uint64_t)count * total <= (1ull << 30);
-}
-
-// The queue order, producer counts and consumer lists of one transform of the plan, from the
-// Stockham index map: output s of group j of pass p (k = j mod Ns) is element (j-k)R + k + s Ns, so
-// element x of pass p's output was written by group ((x >> (logR + logNs)) << logNs) | (x mod Ns),
-// i.e. by tile (that group >> logG).  A tile of pass p+1 with groups j' reads x = j' + r n/R'.
-// Called with the context's lock held.
-static moma_status build_flow(const Plan* pl) {
-  FlowTables& f = pl->flow;
-  if (f.d) return MOMA_OK;
-  const size_t P = pl->passes.size();
-  const uint64_t n = 1ull << pl->logn;
-  uint32_t total = 0;
-  for (size_t p = 0; p < P; ++p) {
-    const PassDesc& d = pl->passes[p];
-    f.tiles[p] = (uint32_t)(n >> (d.logR + d.logG));
-    f.base[p] = total;
-    total += f.tiles[p];
-  }
-  f.total = total;
-  std::vector<std::vector<uint32_t>> prods(total);  // producers (pass-local tiles) of every tile
-  std::vector<uint32_t> stamp;
-  for (size_t p = 0; p + 1 < P; ++p) {
-    const PassDesc& d = pl->passes[p];
-    const PassDesc& dn = pl->passes[p + 1];
-    stamp.assign(f.tiles[p], 0xffffffffu);
-    const uint64_t nR = n >> dn.logR, Gn = 1ull << dn.logG, Rn = 1ull << dn.logR;
-    const uint64_t ns_mask = (1ull << d.logNs) - 1;
-    for (uint32_t c = 0; c < f.tiles[p + 1]; ++c) {
-      std::vector<uint32_t>& v = prods[f.base[p + 1] + c];
-      for (uint64_t g = 0; g < Gn; ++g)
-        for (uint64_t r = 0; r < Rn; ++r) {
-          const uint64_t x = c * Gn + g + r * nR;
-          const uint64_t j = ((x >> (d.logR + d.logNs)) << d.logNs) | (x & ns_mask);
-          const uint32_t pt = (uint32_t)(j >> d.logG);
-          if (stamp[pt] != c) {
-            stamp[pt] = c;
-            v.push_back(pt);
-          }
-        }
-    }
-  }
-  // queue order: the last pass in index order; every earlier pass in the order the next one first
-  // needs its tiles
-  std::vector<uint32_t> order(total), req(total, 0);
-  for (uint32_t i = 0; i < f.tiles[P - 1]; ++i) order[f.base[P - 1] + i] = i;
-  for (size_t p = P - 1; p-- > 0;) {
-    std::vector<char> placed(f.tiles[p], 0);
-    uint32_t k = 0;
-    for (uint32_t pos = 0; pos < f.tiles[p + 1]; ++pos) {
-      const uint32_t c = order[f.base[p + 1] + pos];
-      for (uint32_t pt : prods[f.base[p + 1] + c])
-        if (!placed[pt]) {
-          placed[pt] = 1;
-          order[f.base[p] + k++] = pt;
-        }
-    }
-    for (uint32_t pt = 0; pt < f.tiles[p]; ++pt)
-      if (!placed[pt]) order[f.base[p] + k++] = pt;
-  }
-  // producer counts; consumer lists (CSR over all tiles; the last pass has none)
-  std::vector<uint32_t> off(total + 1, 0);
-  for (size_t p = 0; p + 1 < P; ++p)
-    for (uint32_t c = 0; c < f.tiles[p + 1]; ++c) {
-      req[f.base[p + 1] + c] = (uint32_t)prods[f.base[p + 1] + c].size();
-      for (uint32_t pt : prods[f.base[p + 1] + c]) ++off[f.base[p] + pt + 1];
-    }
-  for (uint32_t i = 0; i < total; ++i) off[i + 1] += off[i];
-  std::vector<uint32_t> idx(off[total]), fill(off.begin(), off.end() - 1);
-  for (size_t p = 0; p + 1 < P; ++p)
-    for (uint32_t c = 0; c < f.tiles[p + 1]; ++c)
-      for (uint32_t pt : prods[f.base[p + 1] + c]) idx[fill[f.base[p] + pt]++] = c;
-  const size_t words = 3 * (size_t)total + 1 + idx.size();
-  uint32_t* d = nullptr;
-  if (cudaMalloc(&d, words * 4) != cudaSuccess) return MOMA_ERR_OOM;
-  std::vector<uint32_t> host;
-  host.reserve(words);
-  host.insert(host.end(), order.begin(), order.end());
-  host.insert(host.end(), req.begin(), req.end());
-  host.insert(host.end(), off.begin(), off.end());
-  host.insert(host.end(), idx.begin(), idx.end());
-  if (cudaMemcpy(d, host.data(), words * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(d);
-    return MOMA_ERR_CUDA;
-  }
-  f.order = d;
-  f.req = d + total;
-  f.cons_off = d + 2 * (size_t)total;
-  f.cons_idx = d + 3 * (size_t)total + 1;
-  f.bytes = words * 4;
-  f.d = d;
-  return MOMA_OK;
-}
-
-// bufs: P-1 intermediate buffers of count*L*n words, one per pass output: unlike the per-pass
-// launches, two passes cannot share a buffer (pass p+2 would overwrite what pass p+1 still reads).
-template <int L, int FE>
-static moma_status launch_flow_l(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
-                                 uint32_t* out, int threads, uint32_t* bufs, uint32_t* ctr, cudaStream_t st) {
-  const FlowTables& f = pl->flow;
-  const size_t P = pl->passes.size();
-  const size_t words = (size_t)L * ((size_t)1 << pl->logn) * count;
-  FlowArgs<L> a;
-  const uint32_t* src = in;
-  int logT = 0;
-  for (size_t i = 0; i < P; ++i) {
-    uint32_t* dst = (i + 1 == P) ? out : bufs + i * words;
-    fill_pass_args<L>(ctx, pl, pl->passes[i], count, src, i == 0 ? in2 : nullptr, dst,
-                      pass_flags(pl, i, P, in2 != nullptr), a.pass[i]);
-    logT = std::max(logT, pl->passes[i].logR + pl->passes[i].logG);
-    a.tiles[i] = f.tiles[i];
-    a.base[i] = f.base[i];
-    src = dst;
-  }
-  a.npass = (uint32_t)P;
-  a.count = (uint32_t)count;
-  a.total = f.total;
-  a.order = f.order;
-  a.req = f.req;
-  a.cons_off = f.cons_off;
-  a.cons_idx = f.cons_idx;
-  a.ctr = ctr;
-  a.head = ctr + (size_t)count * f.total;
-  a.status = ctx->d_status;
-  a.wait_polls = 1ull << 24;
-  const size_t smem = (size_t)L * 4u << logT;
-  auto kern = ntt_flow_kernel<L, FE>;
-  static std::atomic<uint64_t> attr_done{0};  // one bit per device
-  const uint64_t dev_bit = 1ull << (ctx->device & 63);
-  if (!(attr_done.load(std::memory_order_acquire) & dev_bit)) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L * 4 << max_tile_log(L)) !=
-        cudaSuccess)
-      return MOMA_ERR_CUDA;
-    attr_done.fetch_or(dev_bit, std::memory_order_release);
-  }
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) return MOMA_ERR_CUDA;
-  uint64_t grid = (uint64_t)ctx->num_sms * (uint64_t)(occ > 0 ? occ : 1);
-  const uint64_t entries = (uint64_t)count * f.total;
-  if (grid > entries) grid = entries;
-  kern<<<(unsigned)grid, threads, smem, st>>>(a);
-  return cuda_status(cudaGetLastError());
-}
-
-// Every pass of the call in one launch (moma_ntt_flow.cuh), with caller-provided buffers (bufs:
-// P-1 intermediate buffers) and ctr: count * total + 1 words of counters, zeroed here on `st`.
-static moma_status run_plan_flow(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
-                                 uint32_t* out, const moma_config& cfg, uint32_t* bufs, uint32_t* ctr,
-                                 cudaStream_t st) {
-  if (cudaMemsetAsync(ctr, 0, ((size_t)count * pl->flow.total + 1) * 4, st) != cudaSuccess) return MOMA_ERR_CUDA;
-  const bool wide = cfg.engine == 2;
-  const int th = cfg.cta_threads;
-  switch (ctx->L) {
-    case 4: return wide ? launch_flow_l<4, 2>(ctx, pl, count, in, in2, out, th, bufs, ctr, st)
-                        : launch_flow_l<4, 1>(ctx, pl, count, in, in2, out, th, bufs, ctr, st);
-    case 8: return wide ? launch_flow_l<8, 2>(ctx, pl, count, in, in2, out, th, bufs, ctr, st)
-                        : launch_flow_l<8, 1>(ctx, pl, count, in, in2, out, th, bufs, ctr, st);
-    case 12: return wide ? launch_flow_l<12, 2>(ctx, pl, count, in, in2, out, th, bufs, ctr, st)
-                         : launch_flow_l<12, 1>(ctx, pl, count, in, in2, out, th, bufs, ctr, st);
-  }
-  return MOMA_ERR_UNSUPPORTED;
-}
-
-// The plan's passes with intermediate buffers from the stream-ordered pool: one launch per pass, or
-// (schedule field dataflow) all of them in one launch with its counters from the same pool.
+// run_plan_buffers with intermediate buffers from the stream-ordered pool.
 static moma_status run_plan(moma_ctx* ctx, const Plan* pl, size_t count, const uint32_t* in, const uint32_t* in2,
                             uint32_t* out, const moma_config& cfg, cudaStream_t st) {
   const size_t P = pl->passes.size();
   const size_t words = (size_t)ctx->L * ((size_t)1 << pl->logn) * count;
-  if (cfg.dataflow == 1 && flow_eligible(ctx, pl, count, in, in2, out)) {
-    {
-      std::lock_guard<std::mutex> g(ctx->lock);  // the tables are built once per plan, on first use
-      const moma_status rc = build_flow(pl);
-      if (rc) return rc;
-    }
-    // P-1 intermediate buffers and the counters in one allocation
-    const size_t ctr_words = (size_t)count * pl->flow.total + 1;
-    uint32_t* buf = nullptr;
-    if (cudaMallocAsync(&buf, ((P - 1) * words + ctr_words) * 4, st) != cudaSuccess) return MOMA_ERR_OOM;
-    const moma_status rc = run_plan_flow(ctx, pl, count, in, in2, out, cfg, buf, buf + (P - 1) * words, st);
-    cudaFreeAsync(buf, st);
-    return rc;
-  }
   uint32_t* s1 = nullptr;
   uint32_t* s2 = nullptr;
   if (P >= 2 && cudaMallocAsync(&s1, words * 4, st) != cudaSuccess) return MOMA_ERR_OOM;

@@ -110,15 +110,6 @@ extern "C" moma_status moma_autotune(moma_ctx* ctx, int op, size_t n, size_t cou
               if (th <= 128) cands.push_back({engine, tl, r, 0, th, 1});
             }
         }
-    // the one-launch form pays where a call's passes fill few waves of resident CTAs
-    if (!ctx->mont && ctx->L <= 12 && ((uint64_t)count << lg) <= (1ull << 22)) {
-      const size_t m = cands.size();
-      for (size_t i = 0; i < m; ++i) {
-        moma_config c = cands[i];
-        c.dataflow = 1;
-        cands.push_back(c);
-      }
-    }
   } else if (is_vec_op(op)) {
     if (n == 0) return MOMA_ERR_SIZE;
     // full-width contexts: one element per thread, and mulmod's engine 4 (two Montgomery products)

@@ -86,8 +86,7 @@ class moma_job(ctypes.Structure):
 
 class moma_config(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("tile_log", ctypes.c_int), ("max_logr", ctypes.c_int),
-                ("vec_width", ctypes.c_int), ("cta_threads", ctypes.c_int), ("tight_regs", ctypes.c_int),
-                ("dataflow", ctypes.c_int)]
+                ("vec_width", ctypes.c_int), ("cta_threads", ctypes.c_int), ("tight_regs", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -286,9 +285,8 @@ def _op(op) -> int:
     return OPS[op] if isinstance(op, str) else int(op)
 
 
-def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0, cta_threads=0, tight_regs=0,
-                        dataflow=0):
-    cfg = moma_config(engine, tile_log, max_logr, vec_width, cta_threads, tight_regs, dataflow)
+def moma_ctx_set_config(ctx, op, n, engine=0, tile_log=0, max_logr=0, vec_width=0, cta_threads=0, tight_regs=0):
+    cfg = moma_config(engine, tile_log, max_logr, vec_width, cta_threads, tight_regs)
     _check(lib().moma_ctx_set_config(ctx, _op(op), n, ctypes.byref(cfg)), "moma_ctx_set_config")
 
 

@@ -3,7 +3,6 @@
 Every schedule must give bit-identical results; the autotuner's choice is checked the
 same way against the oracle.
 """
-import numpy as np
 import pytest
 import torch
 
@@ -196,85 +195,5 @@ def test_autotune_keeps_only_the_winners_plan(gpu):
         gpu.moma_ntt_fwd(ctx, n, dx, dy)
         torch.cuda.synchronize()
         assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
-    finally:
-        gpu.moma_ctx_destroy(ctx)
-
-
-FLOW_CASES = [  # (log2 n, tile_log, max_logr, cta_threads, count): 2 to 6 passes, several transforms
-    (11, 9, 6, 128, 1), (13, 9, 5, 256, 3), (16, 10, 5, 128, 2), (16, 9, 4, 64, 1), (18, 10, 5, 128, 1),
-    (20, 9, 4, 128, 1), (20, 10, 5, 256, 2)]
-
-
-@pytest.mark.parametrize("width", [128, 256, 384])
-def test_ntt_dataflow_matches_per_pass_and_oracle(gpu, width):
-    """All passes of a call in one launch with per-tile dependencies (schedule field dataflow): forward
-    and inverse transforms of 2 to 6 passes and 1 to 3 transforms per call equal the per-pass launches
-    bit for bit, the oracle in full up to 2^16 points and at sampled outputs (Horner) beyond; the round
-    trip returns the input."""
-    p = inputs.prime(width)
-    ctx = gpu.moma_ctx_create(p.q, width)
-    try:
-        for lg, tile, rmax, th, count in FLOW_CASES:
-            n = 1 << lg
-            xs = np.stack([inputs.residues(p.q, p.L, n, seed=lg + 17 * t) for t in range(count)])
-            dx = gpu.to_device(xs)
-            ref, got, back = torch.empty_like(dx), torch.empty_like(dx), torch.empty_like(dx)
-            for op in ("ntt_fwd", "ntt_inv"):
-                gpu.moma_ctx_set_config(ctx, op, n, engine=2, tile_log=tile, max_logr=rmax, cta_threads=th)
-            gpu.moma_ntt_fwd_many(ctx, n, count, dx, ref)
-            for op in ("ntt_fwd", "ntt_inv"):
-                gpu.moma_ctx_set_config(ctx, op, n, engine=2, tile_log=tile, max_logr=rmax, cta_threads=th, dataflow=1)
-            assert gpu.moma_ctx_get_config(ctx, "ntt_fwd", n)["dataflow"] == 1
-            gpu.moma_ntt_fwd_many(ctx, n, count, dx, got)
-            gpu.moma_ntt_inv_many(ctx, n, count, got, back)
-            torch.cuda.synchronize()
-            assert torch.equal(got, ref), (lg, tile, rmax, count)
-            assert torch.equal(back, dx), (lg, tile, rmax, count)
-            xi = inputs.to_ints(xs[count - 1])
-            if lg <= 16:
-                assert inputs.to_ints(gpu.to_host(got[count - 1])) == oracle.ntt_fwd(xi, p.q)
-            else:
-                w = oracle.root_of_unity(p.q, n)
-                for k in (0, 1, n // 2 + 3, n - 1):
-                    assert inputs.to_ints(gpu.to_host(got[count - 1, :, k:k + 1].contiguous()))[0] == \
-                        oracle.ntt_eval_at(xi, p.q, k, w), (lg, k)
-        assert gpu.moma_ctx_sync_status(ctx) == 0
-    finally:
-        gpu.moma_ctx_destroy(ctx)
-
-
-def test_ntt_dataflow_products_negacyclic_and_in_place(gpu):
-    """The one-launch form under the fused cyclic product, the negacyclic transforms, and in-place
-    calls (which keep the per-pass launches): all equal the oracle."""
-    p = inputs.prime(256)
-    ctx = gpu.moma_ctx_create(p.q, 256)
-    try:
-        n = 1 << 12
-        for op in ("ntt_fwd", "ntt_inv", "polymul"):
-            gpu.moma_ctx_set_config(ctx, op, n, engine=2, tile_log=9, max_logr=4, cta_threads=128, dataflow=1)
-        a = inputs.residues(p.q, p.L, n, 41)
-        b = inputs.residues(p.q, p.L, n, 42)
-        da, db = gpu.to_device(a), gpu.to_device(b)
-        dc = torch.empty_like(da)
-        gpu.moma_polymul(ctx, n, da, db, dc)
-        torch.cuda.synchronize()
-        ai, bi = inputs.to_ints(a), inputs.to_ints(b)
-        assert inputs.to_ints(gpu.to_host(dc)) == oracle.polymul_cyclic(ai, bi, p.q)
-        dn = torch.empty_like(da)
-        gpu.moma_ntt_fwd_negacyclic(ctx, n, da, dn)
-        torch.cuda.synchronize()
-        assert inputs.to_ints(gpu.to_host(dn)) == oracle.ntt_fwd_negacyclic(ai, p.q)
-        back = torch.empty_like(dn)
-        gpu.moma_ntt_inv_negacyclic(ctx, n, dn, back)
-        torch.cuda.synchronize()
-        assert torch.equal(back, da)
-        gpu.moma_ntt_inv_negacyclic(ctx, n, dn, dn)  # in place: the per-pass launches
-        torch.cuda.synchronize()
-        assert torch.equal(dn, da)
-        inplace = da.clone()
-        gpu.moma_ntt_fwd(ctx, n, inplace, inplace)
-        torch.cuda.synchronize()
-        assert inputs.to_ints(gpu.to_host(inplace)) == oracle.ntt_fwd(ai, p.q)
-        assert gpu.moma_ctx_sync_status(ctx) == 0
     finally:
         gpu.moma_ctx_destroy(ctx)
