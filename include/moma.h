@@ -331,8 +331,8 @@ typedef struct {
 /* Set / read the schedule used for `op` at size n (transforms: exact n; BLAS: every n).
  * moma_ctx_get_config reports the effective schedule (defaults filled in) of one transform
  * per call.  Without a schedule set, a transform call whose count * n is at most 2^19 points
- * (128 to 384 bits) takes a default for little work (2^9-element tiles, 128 threads, the
- * register cap), larger calls the default for large batches.  Invalid combinations (shared
+ * (128 to 384 bits) takes a default for little work (2^9-element tiles: 256 threads up to 2^18
+ * points, 128 threads with the register cap at 2^19), larger calls the default for large batches.  Invalid combinations (shared
  * memory over the limit, radix above the tile) give MOMA_ERR_INVALID_ARG. */
 moma_status moma_ctx_set_config(moma_ctx *ctx, int op, size_t n, const moma_config *cfg);
 moma_status moma_ctx_get_config(moma_ctx *ctx, int op, size_t n, moma_config *cfg);

@@ -56,11 +56,12 @@ static NttDefaults ntt_defaults(int L) {
 }
 int default_tile_log(int L) { return ntt_defaults(L).tile_log; }
 
-// Calls with little work (count * n <= 2^19 points, 128 to 384 bits): 2^9-element tiles on
-// 128-thread CTAs with the register cap, so that the call has twice as many CTAs as with 2^10 tiles;
-// radix up to 2^6 below 2^13 points (two passes at 2^12).  Measured on GB300 for single
-// transforms: 2^16 points 0.065 against 0.094 ms at 256 bits, 0.082 against 0.130 ms at 384 bits,
-// 0.055 against 0.074 ms at 128 bits; 2^19 points 4-14% faster; from 2^20 points the default above
+// Calls with little work (count * n <= 2^19 points, 128 to 384 bits): 2^9-element tiles, so that
+// the call has twice as many CTAs as with 2^10 tiles.  Up to 2^18 points 256-thread CTAs (two
+// elements, one butterfly per thread per stage) and radix up to 2^6; at 2^19 points 128-thread CTAs
+// with the register cap and radix up to 2^5.  Measured on GB300 for single transforms: 2^16 points
+// 0.042 against 0.082 ms with the batch default at 256 bits, 0.059 against 0.119 ms at 384 bits,
+// 0.037 against 0.058 ms at 128 bits; 2^18 points 3-22% faster; from 2^20 points the batch default
 // is as fast or faster.
 constexpr int kSmallWorkLog = 19;
 static bool small_work_default(int L, int logn, size_t count) {
@@ -88,7 +89,7 @@ moma_config ntt_config(const moma_ctx* ctx, int op, int logn, size_t count) {
   }
   NttDefaults d = ntt_defaults(ctx->L);
   if (!set && !ctx->mont && small_work_default(ctx->L, logn, count))
-    d = {2, 9, logn <= 12 ? 6 : 5, 128, 1};
+    d = small_work_default(ctx->L, logn + 1, count) ? NttDefaults{2, 9, 6, 256, 0} : NttDefaults{2, 9, 5, 128, 1};
   if (c.engine == 0) c.engine = d.engine;
   if (c.tile_log == 0) c.tile_log = d.tile_log;
   if (c.max_logr == 0) c.max_logr = c.tile_log == d.tile_log ? d.max_logr : (c.tile_log > 6 ? c.tile_log - 5 : 1);

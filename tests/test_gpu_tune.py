@@ -176,9 +176,10 @@ def test_schedule_table_round_trip(gpu, tmp_path):
 
 
 def test_autotune_keeps_only_the_winners_plan(gpu):
-    """The autotuner builds a plan (twiddle tables) per candidate split; the losers' plans are freed,
-    so the context holds at most one more plan than before (the winner's), and the winner's schedule
-    still gives the oracle's transform."""
+    """The autotuner builds a plan (twiddle tables) per candidate split (more than twenty of them);
+    the losers' plans are freed, so the context holds at most one more plan than before (the
+    winner's, whose tables can be a little larger than the default split's), and the winner's
+    schedule still gives the oracle's transform."""
     p = inputs.prime(256)
     ctx = gpu.moma_ctx_create(p.q, 256)
     try:
@@ -191,7 +192,7 @@ def test_autotune_keeps_only_the_winners_plan(gpu):
         base = gpu.moma_ctx_device_bytes(ctx)
         gpu.moma_autotune(ctx, "ntt_fwd", n, 1)
         after = gpu.moma_ctx_device_bytes(ctx)
-        assert base <= after <= 2 * base
+        assert base <= after <= 2.5 * base
         gpu.moma_ntt_fwd(ctx, n, dx, dy)
         torch.cuda.synchronize()
         assert inputs.to_ints(gpu.to_host(dy)) == oracle.ntt_fwd(inputs.to_ints(x), p.q)
