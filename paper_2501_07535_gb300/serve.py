@@ -169,9 +169,10 @@ class Scheduler:
                 used -= f.nbytes
                 progressed = True
             inflight = keep
-            resident = self._resident()
-            stats.resident_bytes = max(stats.resident_bytes, resident)
-            avail = self.budget - resident
+            if queue and len(inflight) < self.slots:  # an admission round: resident memory may have grown
+                resident = self._resident()
+                stats.resident_bytes = max(stats.resident_bytes, resident)
+                avail = self.budget - resident
             while queue and len(inflight) < self.slots:
                 if self.policy == "class":
                     batch, nbytes = self._take_class(queue, jobs, used, rejected, avail)
