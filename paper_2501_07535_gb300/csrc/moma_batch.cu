@@ -463,9 +463,15 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     moma_batch_destroy(b);
     return rc;
   }
-  // queue order: level, then job, then sub-transform
+  // queue order: level; within a level the segments with the most work (tiles x L^2) first, so that
+  // the large transforms' passes end early in the level and their next pass never waits at the
+  // level's end (measured 2.2% faster on the uneven 256-job batch than job order; ordering by the
+  // levels left after the segment first gave 1.7%); then job and sub-transform
   std::stable_sort(pend.begin(), pend.end(), [](const PendingSeg& x, const PendingSeg& y) {
-    return std::make_tuple(x.level, x.job, x.sub) < std::make_tuple(y.level, y.job, y.sub);
+    const uint64_t wx = (uint64_t)x.s.ntiles * x.s.L * x.s.L, wy = (uint64_t)y.s.ntiles * y.s.L * y.s.L;
+    if (x.level != y.level) return x.level < y.level;
+    if (wx != wy) return wx > wy;
+    return std::make_tuple(x.job, x.sub) < std::make_tuple(y.job, y.sub);
   });
   if (cudaMallocAsync(&b->d_args, std::max<size_t>(ab.bytes.size(), 16), ss) != cudaSuccess ||
       cudaMallocAsync(&b->d_segs, std::max<size_t>(pend.size(), 1) * sizeof(Seg), ss) != cudaSuccess ||
