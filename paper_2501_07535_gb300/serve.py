@@ -77,15 +77,17 @@ class Scheduler:
     policy "class": the head of the queue opens the micro-batch and fixes its size class (small or
     large by the executor's cost estimate); the batch then takes, in arrival order from the first
     `lookahead` queued jobs, only jobs of the same class, up to `cost_cap` of estimated work (or the
-    head's own cost, if larger; 1 ms by default: on the served stream at 0.8 x capacity it gave a
-    p99 of 46-48 ms against 60-69 ms with 2 ms, at the same capacity).  A micro-batch completes as a whole, so this keeps small jobs from
+    head's own cost, if larger).  Defaults measured on the served stream at 0.8 x capacity (p99 of
+    three runs; capacity): class threshold and cap 0.5 ms: 38-39 ms, 1467 jobs/s; 1 ms and 1 ms:
+    43-44 ms, 1492 jobs/s; 0.25 ms and 0.25 ms: 33-34 ms, 1413 jobs/s; threshold 0.5 ms with a 2 ms
+    cap: 60-69 ms.  A micro-batch completes as a whole, so this keeps small jobs from
     waiting for a large one launched with them; the head of the queue is always served next, so no
     job waits behind later arrivals of its own class.
     """
 
     def __init__(self, executor, budget_bytes: int = BUDGET_BYTES, slots: int = 4, max_batch_jobs: int = 64,
                  clock=time.perf_counter, idle_sleep_s: float = 20e-6, policy: str = "fifo",
-                 large_cost: float = 5e-4, cost_cap: float = 1e-3, lookahead: int = 512):
+                 large_cost: float = 5e-4, cost_cap: float = 5e-4, lookahead: int = 512):
         if policy not in ("fifo", "class"):
             raise ValueError("policy must be 'fifo' or 'class'")
         self.ex = executor
