@@ -48,3 +48,24 @@ def test_vec_roofline_additions_are_byte_bound():
     assert r["bound"] == "hbm" and r["products_t_achieved"] == 0
     assert r["hbm_gbs_achieved"] == pytest.approx(12 * 8 * (1 << 24) / 1e-3 / 1e9, abs=0.1)
     assert math.isclose(r["frac"], 12 * 8 * (1 << 24) / 6657.6e9 / 1e-3, rel_tol=1e-3)
+
+
+def test_headline_holds_every_part_of_the_metric():
+    """The headline block names the transform rate and its fraction, the mulmod rate and its
+    fraction, batched/plain, served/plain with p50 and the median and worst p99, and the C1
+    latency (the faster of the default and the tuned schedule)."""
+    r = {"value": 4276.0, "roofline": {"frac": 0.606, "mulmod": {"gelem_s": 39.0, "frac": 0.552}},
+         "e2e": {"value": 4429.0}, "batched_vs_plain": {"speedup": 1.37},
+         "served": {"served_over_plain": 1.05, "p50_ms": 4.7, "p99_ms_median": 37.6, "p99_ms_max": 40.4,
+                    "open_loop": {"p99_ms_runs": [40.4, 37.6, 37.5]}},
+         "c1_single_ntt": {"us_per_call": 23.3, "tuned_us_per_call": 23.4}, "cpu_baseline": {"value": 1.53}}
+    h = bench.headline(r)
+    assert h["ntt_per_s"] == 4276.0 and h["ntt_roofline_frac"] == 0.606
+    assert h["mulmod_gelem_s"] == 39.0 and h["mulmod_roofline_frac"] == 0.552
+    assert h["batched_over_plain"] == 1.37 and h["served_over_plain"] == 1.05
+    assert (h["served_p50_ms"], h["served_p99_ms_median"], h["served_p99_ms_max"]) == (4.7, 37.6, 40.4)
+    assert h["served_p99_ms_runs"] == [40.4, 37.6, 37.5]
+    assert h["c1_latency_us"] == 23.3 and h["e2e_ntt_per_s"] == 4429.0
+    # without the optional sections the block still carries the two kernel rates
+    h2 = bench.headline({k: r[k] for k in ("value", "roofline", "e2e")})
+    assert set(h2) == {"ntt_per_s", "ntt_roofline_frac", "e2e_ntt_per_s", "mulmod_gelem_s", "mulmod_roofline_frac"}
