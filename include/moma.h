@@ -332,8 +332,11 @@ typedef struct {
  * moma_ctx_get_config reports the effective schedule (defaults filled in) of one transform
  * per call.  Without a schedule set, a transform call whose count * n is at most 2^19 points
  * (128 to 384 bits) takes a default for little work (2^9-element tiles: 256 threads up to 2^18
- * points, 128 threads with the register cap at 2^19), larger calls the default for large batches.  Invalid combinations (shared
- * memory over the limit, radix above the tile) give MOMA_ERR_INVALID_ARG. */
+ * points, 128 threads with the register cap at 2^19); at 768 bits up to 2^16 points 2^9 tiles
+ * and at 2^17 points 2^10 tiles (256 threads); larger calls take the default for large batches.
+ * Transforms of a batch (moma_batch_create) that run with the per-call kernels take the schedule
+ * of one transform.  Invalid combinations (shared memory over the limit, radix above the tile)
+ * give MOMA_ERR_INVALID_ARG. */
 moma_status moma_ctx_set_config(moma_ctx *ctx, int op, size_t n, const moma_config *cfg);
 moma_status moma_ctx_get_config(moma_ctx *ctx, int op, size_t n, moma_config *cfg);
 

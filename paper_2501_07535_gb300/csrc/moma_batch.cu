@@ -359,9 +359,10 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     }
     const int lg = log2_n(jb.n);
     if (lg < 1 || lg > kMaxLogN) return MOMA_ERR_SIZE;
-    moma_config cfg = ntt_config(ctx, jb.op, lg);
-    // jobs run with the per-call kernels (768 bits, full-width moduli) keep their per-call schedule
+    // jobs run with the per-call kernels (768 bits, full-width moduli) keep the schedule of a
+    // per-call transform (one transform: the little-work default applies)
     const bool per_call = !batch_tile_kind(ctx);
+    moma_config cfg = ntt_config(ctx, jb.op, lg, per_call ? 1 : 0);
     const int tl = per_call ? cfg.tile_log : std::min(cfg.tile_log, kBatchTileLog);
     const int rmax = per_call ? cfg.max_logr : std::min(cfg.max_logr, tl);
     Plan* pl = nullptr;
@@ -419,7 +420,7 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
       d.out = jb.out;
       d.scratch = base;
       d.w = w;
-      if (jb.op <= MOMA_OP_POLYMUL) d.cfg = ntt_config(ctx, jb.op, log2_n(jb.n));
+      if (jb.op <= MOMA_OP_POLYMUL) d.cfg = ntt_config(ctx, jb.op, log2_n(jb.n), 1);
       b->deferred.push_back(d);
     } else if (jb.op == MOMA_OP_NTT_FWD || jb.op == MOMA_OP_NTT_INV) {
       const Plan* pl = jb.op == MOMA_OP_NTT_FWD ? fwd[j] : inv[j];

@@ -63,10 +63,30 @@ int default_tile_log(int L) { return ntt_defaults(L).tile_log; }
 // 0.042 against 0.082 ms with the batch default at 256 bits, 0.059 against 0.119 ms at 384 bits,
 // 0.037 against 0.058 ms at 128 bits; 2^18 points 3-22% faster; from 2^20 points the batch default
 // is as fast or faster.
-constexpr int kSmallWorkLog = 19;
-static bool small_work_default(int L, int logn, size_t count) {
-  if (count == 0 || (L != 4 && L != 8 && L != 12)) return false;
-  return logn + (count > 1 ? 64 - __builtin_clzll((unsigned long long)(count - 1)) : 0) <= kSmallWorkLog;
+// At 768 bits (one 256-thread CTA per SM) a call of up to 2^16 points takes 2^9 tiles with radix up
+// to 2^7 and one of 2^17 points 2^10 tiles with radix up to 2^6: a CTA's latency sets the time of
+// such a call, and smaller tiles spread it over more SMs.  Measured on GB300: 2^12 points 0.110
+// against 0.310 ms, 2^16 points 0.160 against 0.441 ms (also 2^12 x 16 transforms: 0.111 against
+// 0.309 ms), 2^17 points 0.280 against 0.468 ms; from 2^18 points the 2^11 tiles are as fast or
+// faster (within 5% either way up to 2^22).
+static int work_log(int logn, size_t count) {  // ceil(log2(count * n)); -1 when count is unknown (0)
+  if (count == 0) return -1;
+  return logn + (count > 1 ? 64 - __builtin_clzll((unsigned long long)(count - 1)) : 0);
+}
+static bool small_work_default(int L, int logn, size_t count, NttDefaults& d) {
+  const int wl = work_log(logn, count);
+  if (wl < 0) return false;
+  if (L == 4 || L == 8 || L == 12) {
+    if (wl > 19) return false;
+    d = wl <= 18 ? NttDefaults{2, 9, 6, 256, 0} : NttDefaults{2, 9, 5, 128, 1};
+    return true;
+  }
+  if (L == 24) {
+    if (wl > 17) return false;
+    d = wl <= 16 ? NttDefaults{1, 9, 7, 256, 0} : NttDefaults{1, 10, 6, 256, 0};
+    return true;
+  }
+  return false;
 }
 
 // Largest tile that fits the 227 KiB of shared memory one CTA may use.
@@ -88,8 +108,7 @@ moma_config ntt_config(const moma_ctx* ctx, int op, int logn, size_t count) {
     }
   }
   NttDefaults d = ntt_defaults(ctx->L);
-  if (!set && !ctx->mont && small_work_default(ctx->L, logn, count))
-    d = small_work_default(ctx->L, logn + 1, count) ? NttDefaults{2, 9, 6, 256, 0} : NttDefaults{2, 9, 5, 128, 1};
+  if (!set && !ctx->mont) small_work_default(ctx->L, logn, count, d);
   if (c.engine == 0) c.engine = d.engine;
   if (c.tile_log == 0) c.tile_log = d.tile_log;
   if (c.max_logr == 0) c.max_logr = c.tile_log == d.tile_log ? d.max_logr : (c.tile_log > 6 ? c.tile_log - 5 : 1);

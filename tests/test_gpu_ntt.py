@@ -282,3 +282,40 @@ def test_ntt_small_and_large_work_defaults(gpu, ctxs, width):
     gpu.moma_ntt_inv_many(ctxs[width], n, 4, small[:4], back[:4])
     torch.cuda.synchronize()
     assert torch.equal(back[:4], dx[:4])
+
+
+def test_ntt_768bit_little_work_defaults(gpu, ctxs):
+    """768 bits: calls of up to 2^16 points take 2^9 tiles, of 2^17 points 2^10 tiles, larger ones
+    2^11 tiles.  The same transforms through calls on either side of each bound give identical
+    outputs, equal to the oracle's (first transform); 2^17 points against a context held to the
+    2^11-tile schedule, and the round trip."""
+    w = 768
+    ctx = ctxs[w]
+    assert [gpu.moma_ctx_get_config(ctx, "ntt_fwd", 1 << lg)["tile_log"] for lg in (12, 16, 17, 18, 22)] == \
+        [9, 9, 10, 11, 11]
+    p = inputs.prime(w)
+    n = 1 << 14
+    xs = np.stack([inputs.residues(p.q, p.L, n, seed=300 + t) for t in range(16)])
+    dx = gpu.to_device(xs)
+    small, large = torch.empty_like(dx), torch.empty_like(dx)
+    for t in range(0, 16, 4):
+        gpu.moma_ntt_fwd_many(ctx, n, 4, dx[t:t + 4], small[t:t + 4])  # 2^16 points: 2^9 tiles
+    gpu.moma_ntt_fwd_many(ctx, n, 16, dx, large)                       # 2^18 points: 2^11 tiles
+    torch.cuda.synchronize()
+    assert torch.equal(small, large)
+    assert inputs.to_ints(gpu.to_host(small[0])) == oracle.ntt_fwd(inputs.to_ints(xs[0]), p.q)
+    n17 = 1 << 17
+    x17 = gpu.to_device(inputs.residues(p.q, p.L, n17, seed=317))
+    y17, z17, back = torch.empty_like(x17), torch.empty_like(x17), torch.empty_like(x17)
+    gpu.moma_ntt_fwd(ctx, n17, x17, y17)  # 2^10 tiles, radix up to 2^6
+    held = gpu.moma_ctx_create(p.q, w)
+    try:
+        gpu.moma_ctx_set_config(held, "ntt_fwd", n17, engine=1, tile_log=11, max_logr=7, cta_threads=256)
+        gpu.moma_ntt_fwd(held, n17, x17, z17)
+        gpu.moma_ntt_inv(ctx, n17, y17, back)
+        torch.cuda.synchronize()
+        assert torch.equal(y17, z17)
+        assert torch.equal(back, x17)
+        assert gpu.moma_ctx_sync_status(ctx) == 0
+    finally:
+        gpu.moma_ctx_destroy(held)
