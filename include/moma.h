@@ -245,7 +245,10 @@ typedef struct moma_batch moma_batch;
  * one persistent launch: a grid of resident CTAs takes tiles (one pass of one transform,
  * or a slice of one vector op) in dependency order from a device counter; the pointwise
  * product of a cyclic product is fused into the first pass of its inverse.  Job pointers
- * are fixed at creation; refill the same input buffers between runs.  Synchronous. */
+ * are fixed at creation; refill the same input buffers between runs.  Returns once the
+ * batch's descriptors are queued for upload on a library-owned stream (new twiddle tables are
+ * built before it returns); every run waits for that upload on its own stream (a stream wait,
+ * or a host wait when the caller is capturing the stream into a graph). */
 moma_status moma_batch_create(const moma_job *jobs, int njobs, moma_batch **out);
 
 /* Run the batch on `stream` (asynchronous).  The first run launches directly; on a

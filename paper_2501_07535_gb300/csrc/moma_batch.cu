@@ -21,6 +21,7 @@
 // per-call kernels right after it, on the same stream and inside the same CUDA graph.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <tuple>
@@ -195,12 +196,16 @@ struct moma_batch {
   size_t smem = 0;
   int grid = 0;
   uint64_t wait_polls = kDefaultWaitPolls;
+  // one device block holds the small arrays below (filled by one copy at creation)
+  uint8_t* d_block = nullptr;
   Seg* d_segs = nullptr;
   uint32_t* d_tile_seg = nullptr;  // segment index of every tile
   uint8_t* d_args = nullptr;
   uint32_t* d_ctr = nullptr;
   int* d_status = nullptr;
   uint32_t* d_scratch = nullptr;
+  cudaEvent_t ready = nullptr;  // recorded after the creation's upload on the set-up stream
+  bool ready_seen = false;      // the host has seen `ready` complete
   cudaGraphExec_t graph = nullptr;
   bool dirty = false;  // descriptors changed since upload
 };
@@ -327,6 +332,46 @@ moma_status add_transform(const moma_ctx* ctx, const Plan* pl, int job, int sub,
   }
   *total_tiles = before;
   return MOMA_OK;
+}
+
+// CTAs of the persistent kernel that fit the device at once with `smem` bytes of shared memory
+// each (every CTA resident: the dependency waits rely on it); the kernel attribute is set once
+// per device and the occupancy kept per (device, shared memory size).  0 on a CUDA error.
+int resident_grid(int dev, size_t smem) {
+  static std::mutex lock;
+  static uint64_t attr_done = 0;
+  static std::map<std::pair<int, size_t>, int> grids;
+  std::lock_guard<std::mutex> g(lock);
+  const auto key = std::make_pair(dev, smem);
+  const auto it = grids.find(key);
+  if (it != grids.end()) return it->second;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_done & bit)) {
+    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(12 * 4 << kBatchTileLog)) !=
+        cudaSuccess)
+      return 0;
+    attr_done |= bit;
+  }
+  int occ = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ <= 0)
+    return 0;
+  grids[key] = occ * sms;
+  return occ * sms;
+}
+
+// Order work on `st` after the creation's upload: a stream wait on the event, or, while the
+// caller captures `st` into a graph (an outside event cannot join it), a host wait, once.
+moma_status wait_ready(moma_batch* b, cudaStream_t st) {
+  if (b->ready_seen) return MOMA_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MOMA_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (cudaEventSynchronize(b->ready) != cudaSuccess) return MOMA_ERR_CUDA;
+    b->ready_seen = true;
+    return MOMA_OK;
+  }
+  return cuda_status(cudaStreamWaitEvent(st, b->ready, 0));
 }
 
 }  // namespace
@@ -474,40 +519,50 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     if (wx != wy) return wx > wy;
     return std::make_tuple(x.job, x.sub) < std::make_tuple(y.job, y.sub);
   });
-  if (cudaMallocAsync(&b->d_args, std::max<size_t>(ab.bytes.size(), 16), ss) != cudaSuccess ||
-      cudaMallocAsync(&b->d_segs, std::max<size_t>(pend.size(), 1) * sizeof(Seg), ss) != cudaSuccess ||
-      cudaMallocAsync(&b->d_ctr, (1 + counter) * sizeof(uint32_t), ss) != cudaSuccess ||
-      cudaMallocAsync(&b->d_status, sizeof(int), ss) != cudaSuccess) {
-    moma_batch_destroy(b);
-    return MOMA_ERR_OOM;
-  }
   uint64_t total = 0;
-  for (auto& ps : pend) {
-    ps.s.first = (uint32_t)total;
-    ps.s.args = b->d_args + ps.arg_off;
-    total += ps.s.ntiles;
-    b->segs.push_back(ps.s);
-  }
+  for (const auto& ps : pend) total += ps.s.ntiles;
   if (total >= 0xffffffffull) {
     moma_batch_destroy(b);
     return MOMA_ERR_SIZE;
   }
-  b->total = (uint32_t)total;
-  std::vector<uint32_t> tile_seg((size_t)total);
-  for (size_t si = 0; si < b->segs.size(); ++si)
-    std::fill(tile_seg.begin() + b->segs[si].first, tile_seg.begin() + b->segs[si].first + b->segs[si].ntiles,
-              (uint32_t)si);
-  if (cudaMallocAsync(&b->d_tile_seg, std::max<size_t>(tile_seg.size(), 1) * 4, ss) != cudaSuccess ||
-      (total && cudaMemcpyAsync(b->d_tile_seg, tile_seg.data(), tile_seg.size() * 4, cudaMemcpyHostToDevice, ss) !=
-                    cudaSuccess)) {
+  // one device block: arguments | segments | tile -> segment map | status word | counters, each
+  // part 256-byte aligned; everything before the counters is copied from one host image (the
+  // counters are reset by every run)
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_segs = align(std::max<size_t>(ab.bytes.size(), 16));
+  const size_t o_tseg = o_segs + align(std::max<size_t>(pend.size(), 1) * sizeof(Seg));
+  const size_t o_stat = o_tseg + align(std::max<size_t>((size_t)total, 1) * 4);
+  const size_t o_ctr = o_stat + 256;
+  const size_t block_bytes = o_ctr + align((1 + (size_t)counter) * sizeof(uint32_t));
+  if (cudaMallocAsync(&b->d_block, block_bytes, ss) != cudaSuccess) {
     moma_batch_destroy(b);
     return MOMA_ERR_OOM;
   }
+  b->d_args = b->d_block;
+  b->d_segs = reinterpret_cast<Seg*>(b->d_block + o_segs);
+  b->d_tile_seg = reinterpret_cast<uint32_t*>(b->d_block + o_tseg);
+  b->d_status = reinterpret_cast<int*>(b->d_block + o_stat);
+  b->d_ctr = reinterpret_cast<uint32_t*>(b->d_block + o_ctr);
+  std::vector<uint8_t> img(o_ctr, 0);  // the status word starts at 0
+  uint32_t* tile_seg = reinterpret_cast<uint32_t*>(img.data() + o_tseg);
+  uint64_t first = 0;
+  for (const auto& ps : pend) {
+    Seg sg = ps.s;
+    sg.first = (uint32_t)first;
+    sg.args = b->d_args + ps.arg_off;
+    std::fill(tile_seg + first, tile_seg + first + sg.ntiles, (uint32_t)b->segs.size());
+    first += sg.ntiles;
+    b->segs.push_back(sg);
+  }
+  b->total = (uint32_t)total;
   b->ncounters = counter;
-  if (cudaMemcpyAsync(b->d_args, ab.bytes.data(), ab.bytes.size(), cudaMemcpyHostToDevice, ss) != cudaSuccess ||
-      cudaMemcpyAsync(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, ss) !=
-          cudaSuccess ||
-      cudaMemsetAsync(b->d_status, 0, sizeof(int), ss) != cudaSuccess || cudaStreamSynchronize(ss) != cudaSuccess) {
+  memcpy(img.data(), ab.bytes.data(), ab.bytes.size());
+  memcpy(img.data() + o_segs, b->segs.data(), b->segs.size() * sizeof(Seg));
+  // a copy from pageable memory returns once the image is staged, so `img` may go out of scope;
+  // runs wait for `ready` instead of the host waiting here
+  if (cudaMemcpyAsync(b->d_block, img.data(), o_ctr, cudaMemcpyHostToDevice, ss) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(b->ready, ss) != cudaSuccess) {
     moma_batch_destroy(b);
     return MOMA_ERR_CUDA;
   }
@@ -517,18 +572,12 @@ extern "C" moma_status moma_batch_create(const moma_job* jobs, int njobs, moma_b
     if (jobs[j].op <= MOMA_OP_POLYMUL && batch_tile_kind(jobs[j].ctx))
       smem = std::max(smem, (size_t)jobs[j].ctx->L * 4u << kBatchTileLog);
   b->smem = smem;
-  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(12 * 4 << kBatchTileLog)) !=
-      cudaSuccess) {
+  const int grid = resident_grid(dev, smem);
+  if (grid <= 0) {
     moma_batch_destroy(b);
     return MOMA_ERR_CUDA;
   }
-  int occ = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, smem) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || occ <= 0) {
-    moma_batch_destroy(b);
-    return MOMA_ERR_CUDA;
-  }
-  b->grid = occ * sms;  // every CTA resident at once: the waits rely on it
+  b->grid = grid;  // every CTA resident at once: the waits rely on it
   *out = b;
   return MOMA_OK;
 }
@@ -566,6 +615,8 @@ static moma_status batch_launch(moma_batch* b, cudaStream_t st) {
 extern "C" moma_status moma_batch_run(moma_batch* b, void* stream) {
   if (!b) return MOMA_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  const moma_status wr = wait_ready(b, st);
+  if (wr) return wr;
   if (b->dirty) {
     if (cudaMemcpyAsync(b->d_segs, b->segs.data(), b->segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
@@ -629,9 +680,9 @@ extern "C" moma_status moma_batch_inject_missing_dependency(moma_batch* b) {
 extern "C" void moma_batch_destroy(moma_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->ready) cudaEventDestroy(b->ready);
   cudaStream_t ss = setup_stream(b->device);
-  for (void* p : {(void*)b->d_segs, (void*)b->d_tile_seg, (void*)b->d_args, (void*)b->d_ctr, (void*)b->d_status,
-                  (void*)b->d_scratch})
+  for (void* p : {(void*)b->d_block, (void*)b->d_scratch})
     if (p) cudaFreeAsync(p, ss);
   delete b;
 }
@@ -640,7 +691,8 @@ extern "C" moma_status moma_batch_submit(const moma_job* jobs, int njobs, void* 
   moma_batch* b = nullptr;
   moma_status rc = moma_batch_create(jobs, njobs, &b);
   if (rc) return rc;
-  rc = batch_launch(b, (cudaStream_t)stream);
+  rc = wait_ready(b, (cudaStream_t)stream);
+  if (!rc) rc = batch_launch(b, (cudaStream_t)stream);
   if (!rc && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = MOMA_ERR_CUDA;
   if (!rc) rc = moma_batch_sync_status(b);
   moma_batch_destroy(b);

@@ -109,8 +109,18 @@ def load_primes(path: str = PRIMES_JSON) -> dict[tuple[int, int], Prime]:
     return out
 
 
+_TABLES: dict[str, tuple] = {}  # parsed tables of PRIMES_JSON (Prime is immutable)
+
+
+def _tables() -> tuple:
+    if PRIMES_JSON not in _TABLES:
+        _TABLES[PRIMES_JSON] = (load_primes(PRIMES_JSON), load_full_primes(PRIMES_JSON))
+    return _TABLES[PRIMES_JSON]
+
+
 def prime(width: int, seed: int = 0) -> Prime:
-    return load_primes()[(width, seed)]
+    """The committed (W - 4)-bit prime for (W, seed); the table is read once per process."""
+    return _tables()[0][(width, seed)]
 
 
 def load_full_primes(path: str = PRIMES_JSON) -> dict[tuple[int, int], Prime]:
@@ -126,7 +136,8 @@ def load_full_primes(path: str = PRIMES_JSON) -> dict[tuple[int, int], Prime]:
 
 
 def prime_full(width: int, seed: int = 0) -> Prime:
-    return load_full_primes()[(width, seed)]
+    """The committed full-width (W-bit) prime for (W, seed)."""
+    return _tables()[1][(width, seed)]
 
 
 # ----------------------------------------------------------------------------- residues

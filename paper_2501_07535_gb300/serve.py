@@ -71,23 +71,28 @@ class Scheduler:
     The budget covers what the executor keeps resident (`executor.resident_bytes()`, if it has
     one: tables, operand masters) plus the footprint of every job in flight; a job that does not
     fit waits until batches complete, and a job that could never fit beside the resident memory
-    is refused.
+    is refused.  Each job's footprint and cost estimate are taken once, when the run starts.
 
     policy "fifo": a micro-batch takes jobs from the head of the queue in arrival order.
-    policy "class": the head of the queue opens the micro-batch and fixes its size class (small or
-    large by the executor's cost estimate); the batch then takes, in arrival order from the first
-    `lookahead` queued jobs, only jobs of the same class, up to `cost_cap` of estimated work (or the
-    head's own cost, if larger).  Defaults measured on the served stream at 0.8 x capacity (p99 of
-    three runs; capacity): class threshold and cap 0.5 ms: 38-39 ms, 1467 jobs/s; 1 ms and 1 ms:
-    43-44 ms, 1492 jobs/s; 0.25 ms and 0.25 ms: 33-34 ms, 1413 jobs/s; threshold 0.5 ms with a 2 ms
-    cap: 60-69 ms.  A micro-batch completes as a whole, so this keeps small jobs from
-    waiting for a large one launched with them; the head of the queue is always served next, so no
-    job waits behind later arrivals of its own class.
+    policy "class": jobs queue by size class (small or large by the executor's cost estimate,
+    threshold `large_cost`), each class in arrival order.  The earliest-arrived queued job opens the
+    micro-batch; the batch then takes jobs of its class, in arrival order from the first
+    `lookahead` queued jobs of that class, up to `cost_cap` of estimated work (or the head's own
+    cost, if larger); while more than `backlog_jobs` jobs are queued the cap is `backlog_cost_cap`,
+    so micro-batches grow with the backlog and a burst drains with fewer launches.  A micro-batch
+    completes as a whole, so this keeps small jobs from waiting for a large one launched with them;
+    the earliest queued job is always served next, so no job waits behind later arrivals of its own
+    class.  Defaults measured on the served stream (capacity closed-loop; p99 of three runs at 0.8 x
+    capacity): threshold and cap 0.5 ms, 4 ms beyond 128 queued jobs: 1523 jobs/s, p99 42-43 ms;
+    with the 0.5 ms cap throughout 1486-1494 jobs/s, p99 39-41 ms (at the lower offered rate); beyond
+    32 queued jobs instead of 128: the same capacity, p99 55-60 ms.  Earlier sweeps of the fixed cap:
+    1 ms: p99 43-44 ms, 0.25 ms: 33-34 ms at 5% less capacity, 2 ms: 60-69 ms.
     """
 
     def __init__(self, executor, budget_bytes: int = BUDGET_BYTES, slots: int = 4, max_batch_jobs: int = 64,
                  clock=time.perf_counter, idle_sleep_s: float = 20e-6, policy: str = "fifo",
-                 large_cost: float = 5e-4, cost_cap: float = 5e-4, lookahead: int = 512):
+                 large_cost: float = 5e-4, cost_cap: float = 5e-4, lookahead: int = 64,
+                 backlog_jobs: int = 128, backlog_cost_cap: float = 4e-3):
         if policy not in ("fifo", "class"):
             raise ValueError("policy must be 'fifo' or 'class'")
         self.ex = executor
@@ -100,52 +105,79 @@ class Scheduler:
         self.large_cost = large_cost
         self.cost_cap = cost_cap
         self.lookahead = lookahead
-
-    def _cost(self, job) -> float:
-        f = getattr(self.ex, "cost", None)
-        return f(job) if f else 0.0
+        self.backlog_jobs = backlog_jobs
+        self.backlog_cost_cap = backlog_cost_cap
 
     def _resident(self) -> int:
         f = getattr(self.ex, "resident_bytes", None)
         return int(f()) if f else 0
 
-    def _take_class(self, queue, jobs, used, rejected, avail):
-        """One size-homogeneous micro-batch from the queue (policy "class"); `avail` is the budget
-        left beside the resident memory."""
-        batch, nbytes, cost = [], 0, 0.0
-        skipped = []
-        cls = None
-        cap = self.cost_cap
-        scanned = 0
-        while queue and len(batch) < self.max_batch and scanned < self.lookahead:
-            j = queue.popleft()
-            scanned += 1
-            need = self.ex.footprint(jobs[j])
-            if need > avail:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+    def _take_fifo(self, queue, need, used, rejected, avail):
+        batch, nbytes = [], 0
+        while queue and len(batch) < self.max_batch:
+            j = queue[0]
+            if need[j] > avail:  # can never fit: refuse it (MOMA_ERR_BUDGET)
                 rejected.append(j)
+                queue.popleft()
                 continue
-            c = self._cost(jobs[j])
-            large = c >= self.large_cost
-            if cls is None:  # the head of the queue opens the batch
-                if used + need > avail:
-                    skipped.append(j)
+            if used + nbytes + need[j] > avail:
+                if not batch:
                     self._deferred += 1
-                    break
-                cls = large
-                cap = max(cap, c)
-            elif large != cls or cost + c > cap or used + nbytes + need > avail:
-                skipped.append(j)
-                continue
+                break
             batch.append(j)
-            nbytes += need
-            cost += c
-        queue.extendleft(reversed(skipped))  # untaken jobs keep their order at the front
+            nbytes += need[j]
+            queue.popleft()
+        return batch, nbytes
+
+    def _take_class(self, cq, rank, cost, need, used, rejected, avail):
+        """One size-homogeneous micro-batch (policy "class"); `cq` holds the two class queues,
+        `avail` is the budget left beside the resident memory."""
+        while True:
+            fronts = [q for q in cq if q]
+            if not fronts:
+                return [], 0
+            q = min(fronts, key=lambda d: rank[d[0]])  # the earliest-arrived queued job opens the batch
+            h = q[0]
+            if need[h] > avail:  # can never fit: refuse it (MOMA_ERR_BUDGET)
+                rejected.append(q.popleft())
+                continue
+            if used + need[h] > avail:
+                self._deferred += 1
+                return [], 0
+            break
+        q.popleft()
+        batch, nbytes, total = [h], need[h], cost[h]
+        deep = len(cq[0]) + len(cq[1]) >= self.backlog_jobs  # h was one of the queued jobs
+        cap = max(self.backlog_cost_cap if deep else self.cost_cap, cost[h])
+        kept = []
+        scanned = 0
+        while q and len(batch) < self.max_batch and scanned < self.lookahead:
+            j = q.popleft()
+            scanned += 1
+            if need[j] > avail:
+                rejected.append(j)
+            elif total + cost[j] > cap or used + nbytes + need[j] > avail:
+                kept.append(j)
+            else:
+                batch.append(j)
+                nbytes += need[j]
+                total += cost[j]
+        q.extendleft(reversed(kept))  # untaken jobs keep their order at the front
         return batch, nbytes
 
     def run(self, arrivals, jobs) -> ServeStats:
         n = len(jobs)
         order = sorted(range(n), key=lambda i: arrivals[i])
-        queue = deque()
+        rank = [0] * n
+        for r, i in enumerate(order):
+            rank[i] = r
+        need = [self.ex.footprint(j) for j in jobs]
+        cost_f = getattr(self.ex, "cost", None)
+        cost = [cost_f(j) if cost_f else 0.0 for j in jobs]
+        klass = [1 if c >= self.large_cost else 0 for c in cost]
+        by_class = self.policy == "class"
+        queue = deque()          # fifo policy
+        cq = (deque(), deque())  # class policy: small, large
         inflight: list[_Inflight] = []
         done = [None] * n
         rejected = []
@@ -155,10 +187,15 @@ class Scheduler:
         t0 = self.clock()
         self.ex.start(t0)
         nxt = 0
-        while nxt < n or queue or inflight:
+
+        def queued():
+            return len(cq[0]) + len(cq[1]) if by_class else len(queue)
+
+        while nxt < n or queued() or inflight:
             now = self.clock() - t0
             while nxt < n and arrivals[order[nxt]] <= now:
-                queue.append(order[nxt])
+                j = order[nxt]
+                (cq[klass[j]] if by_class else queue).append(j)
                 nxt += 1
             progressed = False
             keep = []
@@ -172,29 +209,15 @@ class Scheduler:
                 used -= f.nbytes
                 progressed = True
             inflight = keep
-            if queue and len(inflight) < self.slots:  # an admission round: resident memory may have grown
+            if queued() and len(inflight) < self.slots:  # an admission round: resident memory may have grown
                 resident = self._resident()
                 stats.resident_bytes = max(stats.resident_bytes, resident)
                 avail = self.budget - resident
-            while queue and len(inflight) < self.slots:
-                if self.policy == "class":
-                    batch, nbytes = self._take_class(queue, jobs, used, rejected, avail)
+            while queued() and len(inflight) < self.slots:
+                if by_class:
+                    batch, nbytes = self._take_class(cq, rank, cost, need, used, rejected, avail)
                 else:
-                    batch, nbytes = [], 0
-                    while queue and len(batch) < self.max_batch:
-                        j = queue[0]
-                        need = self.ex.footprint(jobs[j])
-                        if need > avail:  # can never fit: refuse it (MOMA_ERR_BUDGET)
-                            rejected.append(j)
-                            queue.popleft()
-                            continue
-                        if used + nbytes + need > avail:
-                            if not batch:
-                                self._deferred += 1
-                            break
-                        batch.append(j)
-                        nbytes += need
-                        queue.popleft()
+                    batch, nbytes = self._take_fifo(queue, need, used, rejected, avail)
                 if not batch:
                     break
                 handle = self.ex.launch([jobs[j] for j in batch])
@@ -205,7 +228,7 @@ class Scheduler:
                 stats.max_concurrent_batches = max(stats.max_concurrent_batches, len(inflight))
                 progressed = True
             if not progressed:
-                if not inflight and not queue and nxt < n:
+                if not inflight and not queued() and nxt < n:
                     wait = arrivals[order[nxt]] - (self.clock() - t0)
                     if wait > 0:
                         time.sleep(min(wait, 0.01))
@@ -235,6 +258,7 @@ class GpuExecutor:
         self.keep = keep_outputs
         self.master_log = master_log
         self._masters = {}
+        self._alphas = {}
         self.outputs = {}
 
     # -- resident operand masters: one seeded master per (modulus, operand); a job's operand is a
@@ -258,6 +282,15 @@ class GpuExecutor:
             if job.n <= N:
                 return m[:, :job.n].contiguous()
             return m.repeat(1, job.n // N)
+
+    def alpha(self, job) -> int:
+        """The axpy scalar of a job (a request carries it as data; here it is drawn from the job's
+        seed once, at prewarm or first use, outside the request path)."""
+        key = (job.width, job.prime_seed, job.seed)
+        a = self._alphas.get(key)
+        if a is None:
+            a = self._alphas[key] = inputs.scalar_residue(inputs.prime(job.width, job.prime_seed).q, job.seed)
+        return a
 
     def resident_bytes(self) -> int:
         """Device memory kept across jobs: the operand masters and every context's tables."""
@@ -292,6 +325,8 @@ class GpuExecutor:
             self._master(j.width, j.prime_seed, 0)
             if j.op not in ("ntt_fwd", "ntt_inv"):
                 self._master(j.width, j.prime_seed, 1)
+            if j.op == "axpy":
+                self.alpha(j)
             key = (j.width, j.prime_seed, j.n, j.op)
             if j.op in ("ntt_fwd", "ntt_inv", "polymul") and key not in seen:
                 seen.add(key)
@@ -322,7 +357,7 @@ class GpuExecutor:
                 out = torch.empty_like(a)
             outs.append(out)
             held += [a, b]
-            alpha = inputs.scalar_residue(inputs.prime(j.width, j.prime_seed).q, j.seed) if j.op == "axpy" else None
+            alpha = self.alpha(j) if j.op == "axpy" else None
             dicts.append({"op": j.op, "ctx": self.ctx.get(j.width, j.prime_seed), "n": j.n, "a": a, "b": b,
                           "out": out, "alpha": alpha})
         h = moma.moma_batch_create(dicts)
@@ -366,8 +401,7 @@ def run_plain(jobs, executor, stream=None):
             elif j.op == "mul":
                 moma.moma_vec_mulmod(c, j.n, a, executor.operand(j, 1, st), o, st)
             else:
-                al = inputs.scalar_residue(inputs.prime(j.width, j.prime_seed).q, j.seed)
-                moma.moma_vec_axpymod(c, j.n, al, a, executor.operand(j, 1, st), o, st)
+                moma.moma_vec_axpymod(c, j.n, executor.alpha(j), a, executor.operand(j, 1, st), o, st)
             del a, o
         e1.record(st)
     e1.synchronize()

@@ -197,3 +197,27 @@ def test_resident_memory_is_charged_to_the_budget():
         big = [inputs.Job(op="mul", width=256, n=300, seed=50)]
         st2 = serve.Scheduler(ResidentExecutor(), budget_bytes=450, slots=4, policy=policy).run([0.0], big)
         assert st2.rejected == 1 and st2.completed == 0, policy
+
+
+def test_class_batches_grow_with_the_backlog():
+    """With more than `backlog_jobs` queued the cost cap is `backlog_cost_cap`: 300 small jobs
+    (0.05 ms each) queued at once leave in 64-job micro-batches (3.2 ms, the job limit) while the
+    queue is deep, then in batches of at most 10 (the 0.5 ms cap) once 128 or fewer are queued."""
+    jobs = [inputs.Job(op="mul", width=256, n=50, seed=i) for i in range(300)]
+    ex = CostExecutor(footprint=lambda j: 1)
+    st = serve.Scheduler(ex, budget_bytes=10**9, slots=1, max_batch_jobs=64, policy="class", large_cost=5e-4,
+                         cost_cap=5e-4, backlog_jobs=128, backlog_cost_cap=4e-3).run([0.0] * 300, jobs)
+    assert st.completed == 300
+    sizes = [len(seeds) for _, _, seeds in ex.launches]
+    assert sizes[:2] == [64, 64]  # 300 and 236 queued
+    queued, deep = 300, []
+    for k in sizes:
+        deep.append(queued > 128)
+        queued -= k
+    assert all(k <= 10 for k, d in zip(sizes, deep) if not d)
+    assert sum(sizes) == 300 and max(sizes) == 64
+    # the same stream with the cap alone never exceeds 10 jobs per micro-batch
+    ex2 = CostExecutor(footprint=lambda j: 1)
+    serve.Scheduler(ex2, budget_bytes=10**9, slots=1, max_batch_jobs=64, policy="class", cost_cap=5e-4,
+                    backlog_jobs=10**6).run([0.0] * 300, jobs)
+    assert max(len(s) for _, _, s in ex2.launches) <= 10
