@@ -200,12 +200,36 @@ struct MontArith {
   }
 };
 
+// Where a pass's tile elements come from and where its outputs go.  `base` is the transform's
+// first word (b * L * n), `pos` the element's position in the transform, `e` its tile slot
+// before the swizzle.  GlobalIO: the transform's buffers in global memory (every per-pass
+// launch, the batch kernel, the first load and the last store of a fused transform), read with
+// L2-only loads so that data written earlier in the same persistent launch by other SMs is never
+// served from a stale L1 line.
+struct GlobalIO {
+  template <int L>
+  __device__ __forceinline__ void get(const NttPassArgs<L>& p, uint64_t base, uint64_t pos, uint32_t e,
+                                      const uint32_t* sm, uint32_t logT, uint32_t (&v)[L]) const {
+    (void)e;
+    (void)sm;
+    (void)logT;
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = __ldcg(p.src + base + pos + (uint64_t)l * p.n);
+  }
+  template <int L>
+  __device__ __forceinline__ void put(const NttPassArgs<L>& p, uint64_t base, uint64_t pos,
+                                      const uint32_t (&v)[L]) const {
+#pragma unroll
+    for (int l = 0; l < L; ++l) p.dst[base + pos + (uint64_t)l * p.n] = v[l];
+  }
+};
+
 // One CTA tile of one Stockham pass: `tile` indexes (transform, group block).  `sm` holds
-// L*R*G words.  Used by the per-pass kernels and by the persistent batch kernel; source data
-// are read with L2-only loads so that data written earlier in the same persistent launch by
-// other SMs is never served from a stale L1 line.
-template <int L, class A>
-__device__ __forceinline__ void ntt_tile_impl(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm) {
+// L*R*G words.  Elements come in through `in` and leave through `out` (GlobalIO for the
+// per-pass kernels and the persistent batch kernel).
+template <int L, class A, class IN = GlobalIO, class OUT = GlobalIO>
+__device__ __forceinline__ void ntt_tile_impl(const NttPassArgs<L>& p, uint32_t tile, uint32_t* sm,
+                                              const IN& in = IN(), const OUT& out = OUT()) {
   const uint32_t R = 1u << p.logR;
   const uint32_t G = 1u << p.logG;
   const uint32_t T = R << p.logG;
@@ -221,20 +245,19 @@ __device__ __forceinline__ void ntt_tile_impl(const NttPassArgs<L>& p, uint32_t 
   for (uint32_t e = threadIdx.x; e < T; e += blockDim.x) {
     const uint32_t r = e >> p.logG, g = e & (G - 1);
     const uint64_t j = j0 + g;
-    const uint64_t idx = base + j + (uint64_t)r * nR;
+    const uint64_t pos = j + (uint64_t)r * nR;
     uint32_t v[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) v[l] = __ldcg(p.src + idx + (uint64_t)l * p.n);
+    in.get(p, base, pos, e, sm, logT, v);
     if (p.flags & F_POINTWISE) {
       uint32_t u[L];
 #pragma unroll
-      for (int l = 0; l < L; ++l) u[l] = __ldcg(p.src2 + idx + (uint64_t)l * p.n);
+      for (int l = 0; l < L; ++l) u[l] = __ldcg(p.src2 + base + pos + (uint64_t)l * p.n);
       A::pointwise(v, u, p.k);
     }
     if (p.flags & F_SCALE) A::mul_fixed(v, p.sc, p.scp, p.k);
     if (p.flags & F_PSI_IN) {
       uint32_t w[L], wp[L];
-      twiddle_load<L>(p.psi, j + (uint64_t)r * nR, w, wp);
+      twiddle_load<L>(p.psi, pos, w, wp);
       A::mul_fixed(v, w, wp, p.k);
     }
     if ((p.flags & F_PRETW) && r != 0 && (j & ns_mask) != 0) {
@@ -286,18 +309,17 @@ __device__ __forceinline__ void ntt_tile_impl(const NttPassArgs<L>& p, uint32_t 
     const uint32_t g = (gh << logGl) + gl;
     const uint64_t j = j0 + g;
     const uint64_t kk = j & ns_mask;
-    const uint64_t addr = base + (j - kk) * R + kk + ((uint64_t)sp << p.logNs);
+    const uint64_t pos = (j - kk) * R + kk + ((uint64_t)sp << p.logNs);
     const uint32_t pr = __brev(sp) >> (32 - p.logR);
     uint32_t v[L];
     tile_load<L>(sm, swz((pr << p.logG) + g, logT), v);
     if (p.flags & F_PSI_OUT) {  // Barrett: [0, 4q) -> [0, 3q)
       uint32_t w[L], wp[L];
-      twiddle_load<L>(p.psi, addr - base, w, wp);
+      twiddle_load<L>(p.psi, pos, w, wp);
       A::mul_fixed(v, w, wp, p.k);
     }
     if (p.flags & F_LAST) A::finish(v, p.k);
-#pragma unroll
-    for (int l = 0; l < L; ++l) p.dst[addr + (uint64_t)l * p.n] = v[l];
+    out.put(p, base, pos, v);
   }
 }
 

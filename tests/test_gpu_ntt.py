@@ -319,3 +319,34 @@ def test_ntt_768bit_little_work_defaults(gpu, ctxs):
         assert gpu.moma_ctx_sync_status(ctx) == 0
     finally:
         gpu.moma_ctx_destroy(held)
+
+
+@pytest.mark.parametrize("width", [128, 256, 384])
+@pytest.mark.parametrize("lg", [10, 11, 12])
+def test_pair_cluster_matches_per_pass(gpu, ctxs, width, lg):
+    """A call of little work (count * n <= 2^15 points, 2^16 at 128 bits) whose plan has two passes
+    of at most 8 tiles runs both passes in one cluster launch (2, 4 or 8 CTAs exchanging through
+    distributed shared memory); the same transforms in one call of 2^17 points run pass by pass
+    with the same plan.  Forward and inverse outputs identical, equal to the oracle (first
+    transform), round trip."""
+    p = inputs.prime(width)
+    n = 1 << lg
+    big, small = (1 << 17) >> lg, (1 << 15) >> lg
+    xs = np.stack([inputs.residues(p.q, p.L, n, seed=700 + t) for t in range(big)])
+    dx = gpu.to_device(xs)
+    y_pass, y_pair = torch.empty_like(dx), torch.empty_like(dx)
+    z_pass, z_pair = torch.empty_like(dx), torch.empty_like(dx)
+    ctx = ctxs[width]
+    gpu.moma_ntt_fwd_many(ctx, n, big, dx, y_pass)
+    gpu.moma_ntt_inv_many(ctx, n, big, y_pass, z_pass)
+    for t in range(0, big, small):
+        gpu.moma_ntt_fwd_many(ctx, n, small, dx[t:t + small], y_pair[t:t + small])
+        gpu.moma_ntt_inv_many(ctx, n, small, y_pass[t:t + small], z_pair[t:t + small])
+    y1 = torch.empty_like(dx[0])
+    gpu.moma_ntt_fwd(ctx, n, dx[big - 1], y1)  # one transform: count 1
+    torch.cuda.synchronize()
+    assert torch.equal(y_pair, y_pass)
+    assert torch.equal(z_pair, z_pass) and torch.equal(z_pass, dx)
+    assert torch.equal(y1, y_pass[big - 1])
+    assert inputs.to_ints(gpu.to_host(y_pair[0])) == oracle.ntt_fwd(inputs.to_ints(xs[0]), p.q)
+    assert gpu.moma_ctx_sync_status(ctx) == 0
