@@ -39,7 +39,7 @@ L = WIDTH // 32
 # DRAM bytes per pass launch of the dominant kernel (ntt_pass_kernel<8>, 16 transforms of 2^20):
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a pass over 8 transforms, x 2;
 # valid for this schedule and kernel version (None otherwise).
-NTT_PASS_TRAFFIC_BYTES = 962_203_648
+NTT_PASS_TRAFFIC_BYTES = 961_867_776
 NTT_PASS_TRAFFIC_SCHEDULE = {"engine": 2, "tile_log": 10, "max_logr": 5, "cta_threads": 128, "tight_regs": 0}
 
 # Integer-multiply peak from the unit counts: the multiply pipe (fmaheavy) of each of the 4 SM
@@ -456,7 +456,8 @@ def measure_e2e(ctx, xs, n, steps, warmup, barrier, chunks=None, nstreams=None):
 
 def run_profile(args):
     """Small cases for ncu captures (each op: one untimed call first, then `steps` calls):
-    ntt: batched forward 2^20-point NTTs (--ntt-batch transforms, --profile-bits wide);
+    ntt: batched forward NTTs of 2^--profile-ntt-logn points (--ntt-batch transforms, --profile-bits
+    wide);
     mul / add / sub / axpy: the vector op on 2^--profile-logn elements at --profile-bits;
     ntt768: 768-bit 2^16 NTTs (batch 8); mont_ntt / mont_mul: the 256-bit NTT and mulmod over a
     full-width modulus (its context's default schedule: Montgomery twiddles, word-based Barrett
@@ -513,7 +514,7 @@ def run_profile(args):
         moma.moma_ctx_destroy(ctx)
         print(json.dumps({"profile": op, "bits": width, "n": vn, "calls": 1 + args.steps, "schedule": cfg}))
         return
-    n = 1 << (16 if op == "ntt768" else LOGN)
+    n = 1 << (16 if op == "ntt768" else args.profile_ntt_logn)
     xs = np.stack([inputs.residues(q, Lw, n, seed=10 + t) for t in range(args.ntt_batch)])
     dx = moma.to_device(xs)
     dy = torch.empty_like(dx)
@@ -917,6 +918,7 @@ def main():
                              "batch", "batch_large"])
     ap.add_argument("--profile-bits", type=int, default=WIDTH, help="container width of the profiled op")
     ap.add_argument("--profile-logn", type=int, default=24, help="log2 elements of the profiled vector op")
+    ap.add_argument("--profile-ntt-logn", type=int, default=LOGN, help="log2 points of the profiled transforms (ntt)")
     ap.add_argument("--profile-tile", type=int, default=0, help="staged tile (log2) of the profiled vector op (0: direct)")
     ap.add_argument("--serve-jobs", type=int, default=10000, help="requests in the served stream (0: skip)")
     ap.add_argument("--quick", action="store_true", help="skip the BLAS table and the transform sweep")
