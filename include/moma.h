@@ -162,7 +162,10 @@ moma_status moma_ntt_inv(moma_ctx *ctx, size_t n, const uint32_t *in, uint32_t *
                          void *stream);
 
 /* `count` independent transforms of length n in one launch sequence: transform t reads
- * in + t*L*n and writes out + t*L*n (each transform limb-major on its own). */
+ * in + t*L*n and writes out + t*L*n (each transform limb-major on its own).  Launches: one
+ * per Stockham pass; a call of little work whose schedule has two passes of at most 8 tiles
+ * (128 to 384 bits, count * n up to 2^15 points, 2^16 at 128 bits) runs both passes in one
+ * launch of thread-block clusters (one cluster per transform), with no intermediate buffers. */
 moma_status moma_ntt_fwd_many(moma_ctx *ctx, size_t n, size_t count, const uint32_t *in,
                               uint32_t *out, void *stream);
 moma_status moma_ntt_inv_many(moma_ctx *ctx, size_t n, size_t count, const uint32_t *in,
