@@ -271,3 +271,28 @@ def test_blas_staged_wait_runs_out(gpu):
         assert gpu.moma_ctx_sync_status(ctx) == 0
     finally:
         gpu.moma_ctx_destroy(ctx)
+
+
+def test_default_stream_is_torchs_current_stream(gpu):
+    """stream=None launches on torch's current stream: the handle the binding passes equals
+    torch.cuda.current_stream() outside and inside a stream context, and a call inside the
+    context is ordered on that stream."""
+    from paper_2501_07535_gb300 import moma
+    assert moma._current_stream_handle() == torch.cuda.current_stream().cuda_stream
+    s = torch.cuda.Stream()
+    p = inputs.prime(256)
+    ctx = gpu.moma_ctx_create(p.q, 256)
+    try:
+        a = gpu.to_device(inputs.residues(p.q, p.L, 1 << 12, seed=1))
+        b = gpu.to_device(inputs.residues(p.q, p.L, 1 << 12, seed=2))
+        c = torch.empty_like(a)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            assert moma._current_stream_handle() == s.cuda_stream != torch.cuda.default_stream().cuda_stream
+            gpu.moma_vec_mulmod(ctx, 1 << 12, a, b, c)
+        s.synchronize()
+        assert inputs.to_ints(gpu.to_host(c)) == oracle.vec_mulmod(inputs.to_ints(gpu.to_host(a)),
+                                                                   inputs.to_ints(gpu.to_host(b)), p.q)
+        assert moma._current_stream_handle() == torch.cuda.current_stream().cuda_stream
+    finally:
+        gpu.moma_ctx_destroy(ctx)
